@@ -1,0 +1,438 @@
+#!/usr/bin/env python3
+"""Throughput of the explicit finite-volume Euler residual + Runge-Kutta step
+(SENSEI hot path, arXiv 2305.18057) on GB300, in cell-updates per second per
+RK stage (interior cells x stages / time; the paper's ssspnt with np = 1 and
+substeps counted is 1e-6 times this, Sec. 6 Eq. ssspnt).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3]
+    python bench.py --impl reference ...     # the CPU oracle, timed on the host
+
+One JSON line on rank 0.  A step is one full SSPRK3 step (ghost fill, time
+step reduction, three fused stencil/update stages, norm finalisation) over
+the whole grid.  With N > 1 (torchrun) every rank advances its own replica
+of the grid on its own GPU: the method has no data-path exchange between
+GPUs in this build ("replicas only"), so scaling is weak and the value is the
+sum over ranks of the cells each advanced, over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage (FP64 vs mixed, at stated error); % HBM roofline"
+UNIT = "cell-updates/s"
+
+WORKLOADS = {
+    # name: (builder, description)
+    "c3": ("periodic3d 256^3: smooth curvilinear periodic map (5% of spacing), Mach 2.5 + 5 Fourier modes (1%), "
+           "MUSCL van Leer + Roe (Harten 0.1), SSPRK3, CFL 0.5"),
+    "c1": "advection2d 128^2: periodic box, Mach 2 at 30 deg + Gaussian bump, MUSCL minmod + Roe, SSPRK3, CFL 0.5",
+    "c2": ("ramp2d 1024x512: 10-deg compression ramp, wall stretching 1.02, Mach 4 inflow (12270 Pa, 217 K), "
+           "MUSCL van Leer + Roe, SSPRK3, CFL 0.5"),
+    "c4": ("lattice3d: 4x4x4 blocks of seeded sizes in {32,48,64,96,128}, ramp-like grid, Mach 3 inflow, "
+           "interface ghost exchange, MUSCL van Leer + Roe, SSPRK3, CFL 0.5"),
+    "c5": ("ramp3d 512^3: 8-deg ramp extruded in k, wall stretching 1.005, Mach 4 inflow (12270 Pa, 217 K), "
+           "MUSCL van Leer + Roe, SSPRK3, CFL 0.5"),
+}
+
+# Algorithmic FP64 operations per cell and stage of the fused stencil kernel
+# (add, sub, mul = 1; fused multiply-add = 2; div, sqrt, rsqrt = 1; compares
+# and sign tests 0), counted from the formulas the kernel evaluates: 3 Roe
+# face fluxes (157 each), 3 directions of MUSCL face states (per limiter),
+# the primitive variables (12), the flux-difference sum (25), the update
+# (17, +10 on the stages that blend U^n) and the norm partials (20 on the
+# first stage).  2D: 2 faces, 2 directions, residual sum 15.
+ROE_FLOPS = 157
+STATE_FLOPS = {"none": 25, "minmod": 30, "vanleer": 45}
+
+
+def alg_flops_per_cell(limiter, two_d, alpha_nonzero, first_stage):
+    nd = 2 if two_d else 3
+    f = nd * ROE_FLOPS + nd * STATE_FLOPS[limiter] + 12 + (15 if two_d else 25) + 17
+    if alpha_nonzero:
+        f += 10
+    if first_stage:
+        f += 20
+    return f
+
+
+def alg_bytes_per_cell(precision, alpha_nonzero, first_stage, two_d):
+    """Bytes the stencil kernel must move per interior cell and launch:
+    read U^(s-1) (40), write U^(s) (40), read U^n when blended (40), face
+    metrics (unit normal + area per face, 4 values x 3 faces) and 1/|Omega|
+    (8), and |Omega| (8) for the conservation sums on the first stage."""
+    nd = 2 if two_d else 3
+    mbytes = 4 if precision == "fp32_flux" else 8
+    b = 40 + 40 + nd * 4 * mbytes + 8
+    if alpha_nonzero:
+        b += 40
+    if first_stage:
+        b += 8
+    return b
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 vector peak derived from the unit counts: 152 SMs x 2 FP64 FMA lanes
+# per SM per clock (the 1.25 TFLOP/s FP64 of GB300 at its 2070 MHz maximum
+# clock) x 2 flops x clock.
+def fp64_peak_tflops(sm_mhz=2070.0):
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), util=float(f[4]), hw=f[6], hwt=f[7], swt=f[8],
+                                 pcap=f[9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r["util"] >= 50] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(load)}
+
+
+# ------------------------------------------------------------- workloads --
+
+def make_workload(name, small=False):
+    from paper_2305_18057_gb300 import workloads as wl
+    if name == "c3":
+        return wl.periodic_3d(n=64 if small else 256)
+    if name == "c1":
+        return wl.advection_2d(n=128)
+    if name == "c2":
+        return wl.ramp_2d(ni=1024, nj=512)
+    if name == "c4":
+        return wl.lattice_3d() if not small else wl.lattice_3d(sizes=(8, 12, 16))
+    if name == "c5":
+        return wl.ramp_3d(n=128 if small else 512)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def gpu_setup(w, precision):
+    import torch
+    from paper_2305_18057_gb300 import sensei, workloads as wl
+    g = sensei.Grid(w.dims, w.nodes, gamma=w.gamma, limiter=wl.LIMITERS[w.limiter], kappa=w.kappa, eps=w.eps,
+                    entropy_fix=w.fix, precision=precision)
+    for b, faces in enumerate(w.bcs):
+        for f in range(4 if w.dims[b][2] == 1 else 6):
+            bc = faces[f]
+            g.set_bc(b, f, bc.type, bc.prim, bc.nbr, bc.nbr_face)
+    Us = []
+    for b in range(len(w.dims)):
+        U = g.new_state(b)
+        g.upload(U, b, w.U0[b])
+        Us.append(U)
+    torch.cuda.synchronize()
+    return g, Us
+
+
+def time_steps(g, Us, steps, rk, cfl, profile=False):
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if profile:
+        g.profile(True)
+        g.profile_read(reset=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        g.rk_step(Us, rk, cfl=cfl)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = g.profile_read(reset=True) if profile else None
+    if profile:
+        g.profile(False)
+    return ms, prof
+
+
+# --------------------------------------------------------------- reference --
+
+def oracle_sample(w_name, steps, warmup):
+    """Time the CPU oracle as it stands (one host thread) on a bounded sample
+    of the workload: a k-slab of the grid (k-periodic) for 3D workloads, the
+    whole grid for 2D ones."""
+    import numpy as np
+    import oracle
+    from paper_2305_18057_gb300 import workloads as wl
+    w = make_workload(w_name) if w_name in ("c1",) else None
+    if w_name == "c3":
+        full = wl.periodic_3d(n=256, nk=16)
+        sample = "SSPRK3 steps of a 256x256x16 k-slab of the 256^3 grid and state (k-periodic)"
+        w = full
+    elif w_name == "c5":
+        w = wl.ramp_3d(ni=512, nj=512, nk=4)
+        sample = "SSPRK3 steps of a 512x512x4 k-slab of the 512^3 ramp grid (k-periodic)"
+    elif w_name == "c4":
+        w = wl.lattice_3d(sizes=(16, 24, 32))
+        sample = "SSPRK3 steps of the 4x4x4 lattice with block sizes drawn from {16,24,32}"
+    elif w_name == "c2":
+        w = wl.ramp_2d(ni=1024, nj=128)
+        sample = "SSPRK3 steps of a 1024x128 (near-wall quarter) version of the 1024x512 ramp grid"
+    else:
+        sample = "SSPRK3 steps of the whole 128^2 grid"
+    og = oracle.OracleGrid(w.dims, w.nodes, gamma=w.gamma, limiter=wl.LIMITERS[w.limiter], kappa=w.kappa,
+                           eps=w.eps, fix=w.fix)
+    for b, faces in enumerate(w.bcs):
+        for f in range(4 if w.dims[b][2] == 1 else 6):
+            bc = faces[f]
+            og.set_bc(b, f, bc.type, bc.prim, bc.nbr, bc.nbr_face)
+    Us = []
+    for b in range(len(w.dims)):
+        U = og.alloc_state(b)
+        og.interior(U, b)[...] = w.U0[b]
+        Us.append(U)
+    for _ in range(warmup):
+        og.rk_step(Us, oracle.RK3_SSP, cfl=w.cfl)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        og.rk_step(Us, oracle.RK3_SSP, cfl=w.cfl)
+    t = time.perf_counter() - t0
+    cells = sum(a * b * c for a, b, c in w.dims)
+    return cells * 3 * steps / t, t, f"{steps} {sample}", cells
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    value, secs, sample, cells = oracle_sample(args.workload, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_for(args.workload),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_for(name):
+    return {"workload": WORKLOADS[name], "l2": "inputs larger than L2 (state >= 0.7 GB)" if name in ("c3", "c4", "c5")
+            else "inputs L2-resident (noted, not an HBM claim)", "parallelism": "replicas"}
+
+
+# -------------------------------------------------------------------- main --
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2305_18057_gb300 import build as libbuild
+    from paper_2305_18057_gb300 import sensei
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank == 0 or world == 1:
+        libbuild.build()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        libbuild.build()
+    torch.cuda.set_device(local)
+    sensei.load()
+
+    w = make_workload(args.workload)
+    two_d = all(d[2] == 1 for d in w.dims)
+    cells = w.cells
+    rk = sensei.RK3_SSP
+    stages = 3
+    g, Us = gpu_setup(w, sensei.FP64)
+    for _ in range(args.warmup):
+        g.rk_step(Us, rk, cfl=w.cfl)
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = vis.split(",")[local] if vis else str(local)
+    clocks = ClockSampler(gpu_index)
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    time.sleep(0.4)
+    ms, prof = time_steps(g, Us, args.steps, rk, w.cfl, profile=True)
+    clk = clocks.stop()
+    units = cells * stages * args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        u = torch.tensor([float(units)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = t.item(), u.item()
+    value = units / (ms / 1e3)
+
+    # the dominant kernel: the fused stencil/update kernel
+    st_ms, st_n, k_launches = prof
+    per_launch_ms = st_ms / max(st_n, 1)
+    alpha_frac = 2.0 / 3.0   # SSPRK3: stages 2 and 3 blend U^n
+    flops = cells * (alg_flops_per_cell(w.limiter, two_d, False, True)
+                     + alg_flops_per_cell(w.limiter, two_d, True, False) * 2) / 3.0
+    byts = cells * (alg_bytes_per_cell("fp64", False, True, two_d)
+                    + 2 * alg_bytes_per_cell("fp64", True, False, two_d)) / 3.0
+    peaks, peak_src = measured_peaks()
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    fp64_peak = fp64_peak_tflops(2070.0)
+    achieved_tf = flops / (per_launch_ms / 1e3) / 1e12
+    roofline = {
+        "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": achieved_tf / fp64_peak, "traffic": None,
+        "kernel": "stencil_kernel<double> (fused MUSCL + Roe + residual + RK stage)",
+        "peak_source": "derived FP64 vector peak: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
+        "alg_flops_per_launch": flops, "kernel_ms_per_launch": per_launch_ms,
+        "hbm": {"achieved_gbs": byts / (per_launch_ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                "frac": byts / (per_launch_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src,
+                "alg_bytes_per_launch": byts},
+    }
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": config_for(args.workload),
+        "ssspnt": value * 1e-6, "gpu_launches": k_launches, "roofline": roofline, "clocks": clk,
+    }
+
+    # end to end through the C ABI with host buffers: every step copies the
+    # state in from pinned host memory, steps, copies the new state and the
+    # norms back
+    Uh = [torch.empty(U.numel(), dtype=torch.float64, pin_memory=True) for U in Us]
+    for a, b_ in zip(Uh, Us):
+        a.copy_(b_)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(args.steps):
+        for a, b_ in zip(Uh, Us):
+            b_.copy_(a, non_blocking=True)
+        g.rk_step(Us, rk, cfl=w.cfl)
+        for a, b_ in zip(Uh, Us):
+            a.copy_(b_, non_blocking=True)
+        g.norms()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ems], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = t.item()
+    state_bytes = sum(U.numel() * 8 for U in Us)
+    line["e2e"] = {"value": units / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                   "d2h_bytes_per_step": state_bytes + 15 * 8}
+
+    # the mixed-precision form on the same workload: FP32 reconstruction and
+    # flux, FP64 state, update and norms; error vs the FP64 path (itself
+    # matched to the oracle) after the same steps from the same state
+    if not args.no_variants:
+        g32, U32 = gpu_setup(w, sensei.FP32_FLUX)
+        g64, U64 = gpu_setup(w, sensei.FP64)
+        for _ in range(args.warmup):
+            g32.rk_step(U32, rk, cfl=w.cfl)
+        ms32, prof32 = time_steps(g32, U32, args.steps, rk, w.cfl, profile=True)
+        n_cmp = args.warmup + args.steps
+        for _ in range(n_cmp):
+            g64.rk_step(U64, rk, cfl=w.cfl)
+        # repeat the mixed run from the start for an exact step count
+        g32b, U32b = gpu_setup(w, sensei.FP32_FLUX)
+        for _ in range(n_cmp):
+            g32b.rk_step(U32b, rk, cfl=w.cfl)
+        torch.cuda.synchronize()
+        errs = []
+        for b in range(len(w.dims)):
+            a64 = g64.interior_view(U64[b], b)
+            a32 = g32b.interior_view(U32b[b], b)
+            errs.append((float(torch.linalg.vector_norm(a32[0] - a64[0])),
+                         float(torch.linalg.vector_norm(a64[0]))))
+        rho_l2 = math.sqrt(sum(e[0] ** 2 for e in errs)) / math.sqrt(sum(e[1] ** 2 for e in errs))
+        v32 = cells * stages * args.steps / (ms32 / 1e3)
+        st32 = prof32[0] / max(prof32[1], 1)
+        b32 = cells * (alg_bytes_per_cell("fp32_flux", False, True, two_d)
+                       + 2 * alg_bytes_per_cell("fp32_flux", True, False, two_d)) / 3.0
+        line["variants"] = {"fp32_flux": {
+            "value": v32, "unit": UNIT, "speedup_vs_fp64": v32 / value if world == 1 else None,
+            "rho_l2_rel_err_vs_fp64": rho_l2, "steps_compared": n_cmp,
+            "roofline": {"bound": "hbm", "achieved": b32 / (st32 / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": b32 / (st32 / 1e3) / 1e9 / peaks["hbm_gbs"],
+                         "kernel_ms_per_launch": st32, "peak_source": peak_src}}}
+        del g32, U32, g64, U64, g32b, U32b
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, secs, sample, _ = oracle_sample(args.workload, 3 if args.workload in ("c3", "c5") else 2, 0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                                "seconds": secs, "host_cpus": os.cpu_count()}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

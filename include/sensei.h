@@ -1,0 +1,214 @@
+/*
+ * sensei.h -- C ABI of the GB300 (sm_103a) library for the explicit
+ * finite-volume Euler residual and Runge-Kutta stage update on structured
+ * (multi)block grids: the data-parallel hot path of the SENSEI solver,
+ * arXiv 2305.18057.
+ *
+ * The problem statement the calls follow (citations are to the paper):
+ *   - the conserved variables Q = (rho, rho u, rho v, rho w, rho e_t) and the
+ *     inviscid normal flux F_{i,n} of Eq. governing (Sec. 2);
+ *   - the multi-block structured grid of Sec. 2;
+ *   - the semi-discrete form |Omega_i| dU/dt + R_h = 0 (Eq. spatial_residual)
+ *     with R_h = sum over the f cell faces of F_{i,n} Delta s - |Omega| S_h
+ *     (Eq. residual; f = 4 in 2D, 6 in 3D);
+ *   - MUSCL extrapolation with a limiter (Eq. flux, Sec. 5);
+ *   - explicit Runge-Kutta marching (Eq. runge_kutta, Sec. 3.2);
+ *   - ghost-cell boundary enforcement kept on the GPU (Sec. 5, "Ghost cell
+ *     extrapolation on the GPU") and a per-iteration residual print (Sec. 4).
+ *
+ * Readings of what the paper leaves open (the flux function, reconstructed
+ * variables, limiter, RK coefficients, time-step rule, ghost rules) are the
+ * documented defaults of each call below.
+ *
+ * Conventions for every call:
+ *   - All state, residual, node and source arrays are CALLER-OWNED device
+ *     memory.  The library never allocates device memory: its scratch
+ *     (metrics, Runge-Kutta stage buffers, reduction partials) lives in a
+ *     caller-allocated workspace handed to sensei_create_grid.
+ *   - Pointer arrays ("one per block") are HOST arrays of DEVICE pointers.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream) except sensei_norms, which synchronises it.
+ *   - Errors: a call returns a sensei_status; nothing throws or aborts
+ *     across the ABI.  Argument errors are detected on the host before any
+ *     launch and leave device memory untouched.  sensei_last_error() gives a
+ *     thread-local message for the last failing call of the calling thread.
+ *   - Threading: a grid may be used by one host thread at a time.
+ *   - Device: the grid belongs to the device that was current when it was
+ *     created; later calls make that device current.
+ */
+#ifndef SENSEI_H
+#define SENSEI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sensei_grid sensei_grid;   /* opaque, library-owned host object */
+typedef void *sensei_stream;              /* a cudaStream_t */
+
+typedef enum {
+    SENSEI_OK = 0,
+    SENSEI_ERR_INVALID_ARG = 1,   /* bad pointer, size, enum, block/face index or layout */
+    SENSEI_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the CUDA error) */
+    SENSEI_ERR_NONPHYSICAL = 3,   /* a kernel met rho <= 0, p <= 0 or a non-finite value */
+    SENSEI_ERR_TIMEOUT = 4,       /* reserved: a bounded device wait gave up */
+    SENSEI_ERR_UNSUPPORTED = 5,   /* valid request this build does not implement */
+    SENSEI_ERR_STATE = 6          /* call out of order (e.g. a boundary face left unset) */
+} sensei_status;
+
+/* Arithmetic of the stencil (reconstruction + flux).  The Runge-Kutta
+ * accumulation, the conservation sums and the residual norms are FP64 in
+ * every mode. */
+typedef enum {
+    SENSEI_FP64 = 0,        /* FP64 state, FP64 flux */
+    SENSEI_FP32_FLUX = 1,   /* FP64 state; reconstruction and flux in FP32 */
+    SENSEI_FP32_STORE = 2   /* FP64 master state U^n; FP32 stage states and FP32 flux */
+} sensei_precision;
+
+/* Ghost-cell rules, 2 ghost layers per boundary face. */
+typedef enum {
+    SENSEI_BC_PERIODIC = 0,     /* copy of the opposite face's interior layers */
+    SENSEI_BC_INFLOW = 1,       /* fixed freestream state (supersonic inflow / farfield) */
+    SENSEI_BC_EXTRAPOLATE = 2,  /* zeroth-order extrapolation (supersonic outflow) */
+    SENSEI_BC_SLIP_WALL = 3,    /* mirror: rho, rho e_t copied, momentum m - 2 (m.n) n */
+    SENSEI_BC_INTERFACE = 4     /* copy of a neighbour block's interior layers */
+} sensei_bc_type;
+
+/* Explicit RK schemes, the optimal strong-stability-preserving ones: the
+ * paper's second-order 2-stage and 4-stage schemes, and the 3-stage scheme. */
+typedef enum {
+    SENSEI_RK2_SSP = 0,     /* SSPRK(2,2) */
+    SENSEI_RK3_SSP = 1,     /* SSPRK(3,3) */
+    SENSEI_RK4_SSP2 = 2     /* SSPRK(4,2): second order, 4 stages */
+} sensei_rk;
+
+typedef enum {
+    SENSEI_LIM_NONE = 0,    /* unlimited kappa scheme */
+    SENSEI_LIM_MINMOD = 1,
+    SENSEI_LIM_VANLEER = 2
+} sensei_limiter;
+
+/* Cells of one block; nk == 1 makes the block two-dimensional (one cell
+ * deep, no k-faces, rho w carried but left unchanged). */
+typedef struct {
+    int ni, nj, nk;
+} sensei_block_desc;
+
+typedef struct {
+    double gamma;           /* ratio of specific heats, e.g. 1.4 */
+    int limiter;            /* sensei_limiter */
+    double kappa;           /* MUSCL kappa of Eq. flux (only matters for SENSEI_LIM_NONE) */
+    double eps;             /* MUSCL epsilon of Eq. flux: 1 second order, 0 first order */
+    double entropy_fix;     /* Harten's fix width delta = entropy_fix * (Roe sound speed); 0 = off */
+    int precision;          /* sensei_precision */
+    int reconstruct_conserved; /* 0: reconstruct primitive (rho, u, v, w, p); 1: conserved Q */
+} sensei_scheme;
+
+/* Where cell (i, j, k), variable v of a block's state lives: element
+ *   offset + v * stride_var + k * stride_k + j * stride_j + i
+ * of an array of `elems` doubles, for i in [-ghost_i, ni + ghost_i),
+ * j in [-ghost_j, nj + ghost_j), k in [-ghost_k, nk + ghost_k).  Rows are
+ * padded so that every row and every variable plane starts on a 32-byte
+ * boundary.  State arrays are allocated by the caller with this layout. */
+typedef struct {
+    long long stride_j, stride_k, stride_var;
+    long long offset;
+    long long elems;
+    int ghost_i, ghost_j, ghost_k;
+    int elem_bytes;
+} sensei_layout;
+
+/* Bytes of device workspace a grid with these blocks and scheme needs. */
+sensei_status sensei_workspace_size(const sensei_block_desc *blocks, int nblocks,
+                                    const sensei_scheme *scheme, size_t *bytes);
+
+/* Create a grid.  nodes[b] is a device array X[3][nk+1][nj+1][ni+1] (FP64,
+ * x then y then z) of block b's node coordinates; a 2D block has two node
+ * planes (z = 0 and z = 1, unit depth).  The face area vectors (half the
+ * cross product of the face diagonals, oriented toward increasing index)
+ * and the cell volumes (divergence theorem on the position vector) are
+ * computed on the device into `workspace` (device memory, >= the size from
+ * sensei_workspace_size, 256-byte aligned), which the caller keeps alive
+ * and unchanged until sensei_destroy_grid.  The node arrays may be freed
+ * once the stream has passed this call.  Boundary faces start unset. */
+sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks,
+                                 const double *const *nodes, const sensei_scheme *scheme,
+                                 void *workspace, size_t workspace_bytes, sensei_stream stream,
+                                 sensei_grid **out);
+
+/* Free the host object (the workspace stays the caller's). */
+sensei_status sensei_destroy_grid(sensei_grid *grid);
+
+/* Layout of block `block`'s state arrays (see sensei_layout). */
+sensei_status sensei_state_layout(const sensei_grid *grid, int block, sensei_layout *out);
+
+/* Boundary rule of face `face` (0 imin, 1 imax, 2 jmin, 3 jmax, 4 kmin,
+ * 5 kmax) of block `block`.  prim (host, 5 doubles rho, u, v, w, p) is
+ * required for SENSEI_BC_INFLOW.  SENSEI_BC_INTERFACE connects to face
+ * nbr_face of block nbr_block, which must be the opposite side of the same
+ * index direction with the same tangential size; orientation must be 0
+ * (tangential indices aligned).  Every face of every block (faces 0-3 in 2D)
+ * must be set before the first fill/residual/step call. */
+sensei_status sensei_set_bc(sensei_grid *grid, int block, int face, int type, const double *prim,
+                            int nbr_block, int nbr_face, int orientation);
+
+/* Fill the two ghost layers of every boundary face of every block of the
+ * states U[b] (Sec. 5, ghost cells on the GPU).  Edge and corner ghosts are
+ * never read by the dimension-by-dimension stencil and are left alone. */
+sensei_status sensei_fill_ghosts(sensei_grid *grid, double *const *U, sensei_stream stream);
+
+/* Fill the ghosts of U, then write the residual R_h of Eq. residual for
+ * every interior cell to R[b], a dense device array R[5][nk][nj][ni] (FP64):
+ *   R = sum over the faces of the cell of F_hat . S_out  -  src
+ * with F_hat the Roe flux (Harten entropy fix) of the MUSCL face states and
+ * S_out the outward area vector.  src[b] (may be NULL, or src itself NULL)
+ * is |Omega| S_h per interior cell in the same layout as R.  Also records
+ * the norms of this R (read them with sensei_norms). */
+sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const *R,
+                              const double *const *src, sensei_stream stream);
+
+/* One explicit Runge-Kutta step of all blocks, in place on U[b]
+ * (Eq. runge_kutta with the 1/|Omega| of Eq. spatial_residual; evaluated in
+ * the equivalent low-storage Shu-Osher form).  If cfl > 0 the step is
+ * dt = cfl * min over cells of |Omega| / sum_d (|u . Sbar_d| + c |Sbar_d|)
+ * evaluated on the device from U^n; otherwise `dt` (> 0) is used.  If
+ * dt_used is not NULL the step's dt is written there (device, 1 double).
+ * The norms of R(U^n) and the sums of |Omega| U^n are recorded for
+ * sensei_norms.  The ghost layers of U are refilled; on return they are
+ * not those of the new state. */
+sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double cfl, double dt,
+                             double *dt_used, sensei_stream stream);
+
+/* Synchronise `stream` and copy out (host arrays of 5 doubles, any may be
+ * NULL) the norms recorded by the last sensei_residual or sensei_rk_step:
+ *   l2[q] = sqrt(sum_c R_q^2 / N), linf[q] = max_c |R_q|, cons[q] = sum_c |Omega_c| U_q
+ * over all N interior cells of all blocks (Sec. 4 "residual print").  Sums
+ * are taken in a fixed order, so results are deterministic.  Returns
+ * SENSEI_ERR_NONPHYSICAL (and clears the flag) if a kernel met a
+ * non-physical or non-finite state since the last call. */
+sensei_status sensei_norms(sensei_grid *grid, double *l2, double *linf, double *cons, sensei_stream stream);
+
+/* Instrumentation (not part of the method).  While enabled (enable != 0),
+ * every launch of the fused stencil kernel (the residual / Runge-Kutta stage
+ * kernel) is bracketed by a CUDA event pair recorded on its own stream, and
+ * every kernel launch the library issues is counted.  Events are created on
+ * first use; do not enable it inside a CUDA-graph capture. */
+sensei_status sensei_profile_enable(sensei_grid *grid, int enable);
+
+/* Synchronise the recorded events and return, for the interval since the
+ * last reset: the summed stencil-kernel time in milliseconds, the number of
+ * stencil launches and the number of all kernel launches (any pointer may be
+ * NULL).  reset != 0 starts a new interval. */
+sensei_status sensei_profile_read(sensei_grid *grid, double *stencil_ms, long long *stencil_launches,
+                                  long long *kernel_launches, int reset);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *sensei_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SENSEI_H */

@@ -1,0 +1,509 @@
+// stencil.cuh -- the fused residual / Runge-Kutta stage kernel.
+//
+// One CTA owns a TI x TJ column of cells and marches up a chunk of k-planes
+// (2.5-D blocking).  Per plane:
+//   P0  primitives W = (rho, u, v, w, p) of the plane, with a 2-cell halo in
+//       i and j, into shared memory (the interior from the per-thread
+//       k-window registers, the halo ring from global memory);
+//   P1  MUSCL face states of every cell for the i and j directions, each
+//       limited slope computed once per cell and direction (Eq. flux; the
+//       limiter-reuse idea of Sec. 5 kept on chip instead of in a global
+//       array);
+//   P2  the Roe flux of every i- and j-face of the tile, once per face, into
+//       shared memory; the k-face above each column in registers;
+//   P3  R = sum over the faces of F.S_out - |Omega| S_h (Eq. residual), then
+//       either R is written out (residual mode) or the Runge-Kutta stage
+//       update out = alpha U^n + beta U^(s-1) - gdt dt R / |Omega| is applied
+//       (Eq. runge_kutta, Shu-Osher form), with FP64 norm partials.
+// The reconstruction/flux arithmetic type is R (double or float); the state,
+// the update and every reduction are FP64.
+#pragma once
+
+#include <math.h>
+
+#include "sensei_internal.cuh"
+
+namespace sensei {
+
+template <typename R>
+struct SmemLayout {
+    // sW[NV][TJ+4][TI+4], sP_i[2][NV][TJ][TI+2], sP_j[2][NV][TJ+2][TI],
+    // sF_i[NV][TJ][TI+1], sF_j[NV][TJ+1][TI], reduction scratch
+    static constexpr int W = NV * (TJ + 4) * (TI + 4);
+    static constexpr int PI = 2 * NV * TJ * (TI + 2);
+    static constexpr int PJ = 2 * NV * (TJ + 2) * TI;
+    static constexpr int FI = NV * TJ * (TI + 1);
+    static constexpr int FJ = NV * (TJ + 1) * TI;
+    static constexpr int elems = W + PI + PJ + FI + FJ;
+    static constexpr int red_doubles = 3 * NV * (NTHREADS / 32);
+    static constexpr size_t bytes = sizeof(R) * (size_t)elems + sizeof(double) * red_doubles + 16;
+};
+
+template <typename R>
+__device__ __forceinline__ R rsqrt_t(R x);
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+
+// conserved -> primitive; true if rho > 0, p > 0 and both finite
+template <typename R>
+__device__ __forceinline__ bool to_prim(const R q[NV], R gm1, R w[NV])
+{
+    R ir = R(1) / q[0];
+    R u = q[1] * ir, v = q[2] * ir, ww = q[3] * ir;
+    R p = gm1 * (q[4] - R(0.5) * (q[1] * u + q[2] * v + q[3] * ww));
+    w[0] = q[0];
+    w[1] = u;
+    w[2] = v;
+    w[3] = ww;
+    w[4] = p;
+    return q[0] > R(0) && p > R(0) && q[0] < R(INFINITY) && p < R(INFINITY);
+}
+
+// MUSCL extrapolation to the two faces of one cell (Eq. flux), per variable:
+//   plus-side state  W_c + d_plus   (left state of face c+1/2)
+//   minus-side state W_c - d_minus  (right state of face c-1/2)
+// Limited: d_plus = d_minus = (eps/2) sigma with sigma the minmod or van Leer
+// slope of the two differences (the printed kappa form reduces to this for a
+// symmetric limiter).  Unlimited: the kappa form,
+//   d_plus  = eps/4 [(1-kappa) dm + (1+kappa) dp],
+//   d_minus = eps/4 [(1+kappa) dm + (1-kappa) dp].
+template <typename R, int LIM>
+__device__ __forceinline__ void face_states(R wm, R w0, R wp, R c1, R c2, R half_eps, R &plus, R &minus)
+{
+    R dm = w0 - wm, dp = wp - w0;
+    if (LIM == SENSEI_LIM_NONE) {
+        plus = w0 + (c1 * dm + c2 * dp);
+        minus = w0 - (c2 * dm + c1 * dp);
+    } else {
+        R s;
+        if (LIM == SENSEI_LIM_MINMOD) {
+            R m = fmin(fabs(dm), fabs(dp));
+            s = (dm * dp > R(0)) ? copysign(m, dm) : R(0);
+        } else {
+            R pr = dm * dp;
+            s = (pr > R(0)) ? R(2) * pr / (dm + dp) : R(0);
+        }
+        R d = half_eps * s;
+        plus = w0 + d;
+        minus = w0 - d;
+    }
+}
+
+// Roe flux through a face of unit normal n and area A between primitive
+// states wl, wr: A/2 [F(wl) + F(wr) - sum_k |lam_k| alpha_k r_k], three-wave
+// form, Harten's entropy fix on the acoustic waves (delta = fix * a).
+template <typename R>
+__device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R ny, R nz, R A, R gm1, R kg,
+                                         R fix, R F[NV])
+{
+    const R rl = wl[0], ul = wl[1], vl = wl[2], zl = wl[3], pl = wl[4];
+    const R rr = wr[0], ur = wr[1], vr = wr[2], zr = wr[3], pr = wr[4];
+    const R vnl = nx * ul + ny * vl + nz * zl;
+    const R vnr = nx * ur + ny * vr + nz * zr;
+    const R rhl = kg * pl + R(0.5) * rl * (ul * ul + vl * vl + zl * zl);   // rho h_t
+    const R rhr = kg * pr + R(0.5) * rr * (ur * ur + vr * vr + zr * zr);
+    const R ml = rl * vnl, mr = rr * vnr;
+    const R psum = pl + pr;
+    R c[NV];
+    c[0] = ml + mr;
+    c[1] = ml * ul + mr * ur + nx * psum;
+    c[2] = ml * vl + mr * vr + ny * psum;
+    c[3] = ml * zl + mr * zr + nz * psum;
+    c[4] = rhl * vnl + rhr * vnr;
+    // Roe average, weights sqrt(rho)
+    const R isl = rsqrt_t(rl), isr = rsqrt_t(rr);
+    const R sl = rl * isl, sr = rr * isr;
+    const R inv = R(1) / (sl + sr);
+    const R wL = sl * inv, wR = sr * inv;
+    const R u = wL * ul + wR * ur, v = wL * vl + wR * vr, w = wL * zl + wR * zr;
+    const R H = (rhl * isl + rhr * isr) * inv;
+    const R rho = sl * sr;
+    const R q2 = u * u + v * v + w * w;
+    const R a2 = gm1 * (H - R(0.5) * q2);
+    const R ia = rsqrt_t(a2);
+    const R a = a2 * ia;
+    const R ia2 = ia * ia;
+    const R vn = nx * u + ny * v + nz * w;
+    const R dr = rr - rl, dp = pr - pl, du = ur - ul, dv = vr - vl, dw = zr - zl, dvn = vnr - vnl;
+    R l1 = fabs(vn - a), l3 = fabs(vn + a);
+    const R l2 = fabs(vn);
+    const R delta = fix * a;
+    if (l1 < delta) l1 = R(0.5) * (l1 * l1 / delta + delta);
+    if (l3 < delta) l3 = R(0.5) * (l3 * l3 / delta + delta);
+    const R rad = rho * a * dvn;
+    const R c1w = l1 * (R(0.5) * (dp - rad) * ia2);
+    const R c3w = l3 * (R(0.5) * (dp + rad) * ia2);
+    const R c2w = l2 * (dr - dp * ia2);
+    const R cs = l2 * rho;
+    const R s13 = c1w + c3w, d13 = c3w - c1w;
+    const R D0 = s13 + c2w;
+    const R g = a * d13 - cs * dvn;
+    R D[NV];
+    D[0] = D0;
+    D[1] = u * D0 + nx * g + cs * du;
+    D[2] = v * D0 + ny * g + cs * dv;
+    D[3] = w * D0 + nz * g + cs * dw;
+    D[4] = H * s13 + a * vn * d13 + R(0.5) * q2 * c2w + cs * (u * du + v * dv + w * dw - vn * dvn);
+    const R h = R(0.5) * A;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) F[q] = h * (c[q] - D[q]);
+}
+
+// The face flux from the two reconstructed states (primitive, or conserved
+// when p.cons is set).
+template <typename R>
+__device__ __forceinline__ void face_flux(R L[NV], R Rt[NV], R nx, R ny, R nz, R A, R gm1, R kg, R fix, int cons,
+                                          R F[NV])
+{
+    if (cons) {
+        R wl[NV], wr[NV];
+        to_prim(L, gm1, wl);
+        to_prim(Rt, gm1, wr);
+        roe_flux(wl, wr, nx, ny, nz, A, gm1, kg, fix, F);
+    } else {
+        roe_flux(L, Rt, nx, ny, nz, A, gm1, kg, fix, F);
+    }
+}
+
+template <typename R>
+struct CellLoader {
+    const double *in;
+    StateLayout L;
+    int ni, nj, nk;
+    __device__ __forceinline__ bool inside(int i, int j, int k) const
+    {
+        return i >= -NG && i < ni + NG && j >= -NG && j < nj + NG && k >= -L.gk && k < nk + L.gk;
+    }
+    __device__ __forceinline__ void raw(int i, int j, int k, double q[NV]) const
+    {
+        if (inside(i, j, k)) {
+            const double *c = in + L.off + (long long)k * L.sk + (long long)j * L.sj + i;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) q[v] = __ldg(c + v * L.sv);
+        } else {   // outside the ghosted box: a harmless state, never used by a valid face
+            q[0] = 1.0;
+            q[1] = q[2] = q[3] = 0.0;
+            q[4] = 2.5;
+        }
+    }
+};
+
+// Convert a loaded cell to the reconstructed variables; flag non-physical
+// interior cells.
+template <typename R>
+__device__ __forceinline__ void to_recon(const double qd[NV], R gm1, int cons, bool interior, unsigned *err, R out[NV])
+{
+    R q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = (R)qd[v];
+    R w[NV];
+    bool ok = to_prim(q, gm1, w);
+    if (interior && !ok) atomicOr(err, ERR_NONPHYSICAL);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = cons ? q[v] : w[v];
+}
+
+template <typename R, int LIM, bool TWO_D>
+__global__ void __launch_bounds__(NTHREADS, 1) stencil_kernel(const StencilParams<R> p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using SL = SmemLayout<R>;
+    R *sW = reinterpret_cast<R *>(smem_raw);
+    R *sPi = sW + SL::W;
+    R *sPj = sPi + SL::PI;
+    R *sFi = sPj + SL::PJ;
+    R *sFj = sFi + SL::FI;
+    double *sRed = reinterpret_cast<double *>(sFj + SL::FJ + ((SL::elems * sizeof(R)) % 8 ? 1 : 0));
+
+    constexpr int WP = TI + 4;                 // sW row pitch
+    constexpr int WPL = (TJ + 4) * WP;         // sW variable plane
+    auto W_at = [&](int v, int r, int c) -> R & { return sW[v * WPL + (r + 2) * WP + (c + 2)]; };
+    constexpr int PIP = TI + 2, PIV = TJ * PIP, PIS = NV * PIV;
+    constexpr int PJP = TI, PJV = (TJ + 2) * PJP, PJS = NV * PJV;
+    constexpr int FIP = TI + 1, FIV = TJ * FIP;
+    constexpr int FJP = TI, FJV = (TJ + 1) * FJP;
+
+    const int t = threadIdx.x;
+    const int ti = t % TI, tj = t / TI;
+    int item = blockIdx.x;
+    const int tile_i = item % p.tiles_i;
+    item /= p.tiles_i;
+    const int tile_j = item % p.tiles_j;
+    const int chunk = item / p.tiles_j;
+    const int i0 = tile_i * TI, j0 = tile_j * TJ;
+    const int k0 = TWO_D ? 0 : chunk * p.kchunk;
+    const int k1 = TWO_D ? 1 : min(k0 + p.kchunk, p.nk);
+    const int ci = i0 + ti, cj = j0 + tj;
+    const bool col_valid = ci < p.ni && cj < p.nj;
+
+    const R gm1 = p.gamma - R(1);
+    const R kg = p.gamma / gm1;
+    const R c1 = p.eps * (R(1) - p.kappa) / R(4);
+    const R c2 = p.eps * (R(1) + p.kappa) / R(4);
+    const R half_eps = p.eps / R(2);
+    const int cons = p.cons;
+
+    CellLoader<R> ld{p.in, p.L, p.ni, p.nj, p.nk};
+    const bool update = p.out != nullptr;
+    const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
+
+    double nsq[NV], nmax[NV], ncons[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) nsq[v] = nmax[v] = ncons[v] = 0.0;
+
+    // per-thread k-window of the own column: centre plane, the two above,
+    // the plus-side k-state of the centre plane, the flux of its lower k-face
+    R Wc[NV], W1[NV], W2[NV], Pp[NV], Fkm[NV];
+    if (!TWO_D) {
+        double q[NV];
+        R Wm2[NV], Wm1[NV];
+        ld.raw(ci, cj, k0 - 2, q);
+        to_recon(q, gm1, cons, false, p.err, Wm2);
+        ld.raw(ci, cj, k0 - 1, q);
+        to_recon(q, gm1, cons, false, p.err, Wm1);
+        ld.raw(ci, cj, k0, q);
+        to_recon(q, gm1, cons, col_valid, p.err, Wc);
+        ld.raw(ci, cj, k0 + 1, q);
+        to_recon(q, gm1, cons, col_valid && k0 + 1 < p.nk, p.err, W1);
+        ld.raw(ci, cj, k0 + 2, q);
+        to_recon(q, gm1, cons, col_valid && k0 + 2 < p.nk, p.err, W2);
+        // face k0-1/2: left state from plane k0-1, right state from plane k0
+        R Lk[NV], Rk[NV], dummy;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            face_states<R, LIM>(Wm2[v], Wm1[v], Wc[v], c1, c2, half_eps, Lk[v], dummy);
+            face_states<R, LIM>(Wm1[v], Wc[v], W1[v], c1, c2, half_eps, Pp[v], Rk[v]);
+        }
+        long long fk = (long long)k0 * p.ml.mplane + (long long)min(cj, p.nj - 1) * p.ml.mpitch + min(ci, p.ni - 1);
+        face_flux(Lk, Rk, p.fm.n[2][0][fk], p.fm.n[2][1][fk], p.fm.n[2][2][fk], p.fm.n[2][3][fk], gm1, kg, p.fix,
+                  cons, Fkm);
+    }
+
+    for (int k = k0; k < k1; ++k) {
+        // ---- P0: the centre plane with its halo into shared memory
+        double pre[NV];
+        if (!TWO_D) {
+            ld.raw(ci, cj, k + 3, pre);   // prefetch the plane entering the window
+#pragma unroll
+            for (int v = 0; v < NV; ++v) W_at(v, tj, ti) = Wc[v];
+            // halo ring: 2 columns each side of the TJ rows, 2 rows each side of the TI columns
+            for (int e = t; e < 4 * TJ + 4 * TI; e += NTHREADS) {
+                int r, c;
+                if (e < 4 * TJ) {
+                    r = e >> 2;
+                    int s = e & 3;
+                    c = s < 2 ? s - 2 : TI + s - 2;
+                } else {
+                    int e2 = e - 4 * TJ;
+                    int s = e2 / TI;
+                    c = e2 % TI;
+                    r = s < 2 ? s - 2 : TJ + s - 2;
+                }
+                double q[NV];
+                R w[NV];
+                ld.raw(i0 + c, j0 + r, k, q);
+                to_recon(q, gm1, cons, false, p.err, w);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) W_at(v, r, c) = w[v];
+            }
+        } else {
+            for (int e = t; e < (TJ + 4) * (TI + 4); e += NTHREADS) {
+                int r = e / (TI + 4) - 2, c = e % (TI + 4) - 2;
+                bool corner = (r < 0 || r >= TJ) && (c < 0 || c >= TI);
+                if (corner) continue;
+                double q[NV];
+                R w[NV];
+                int gi = i0 + c, gj = j0 + r;
+                ld.raw(gi, gj, 0, q);
+                to_recon(q, gm1, cons, gi >= 0 && gi < p.ni && gj >= 0 && gj < p.nj && r >= 0 && r < TJ && c >= 0 &&
+                                           c < TI,
+                         p.err, w);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) W_at(v, r, c) = w[v];
+            }
+        }
+        __syncthreads();
+
+        // ---- P1: face states, i direction (cells -1..TI of every row) and
+        //      j direction (rows -1..TJ of every column)
+        for (int e = t; e < TJ * (TI + 2) + (TJ + 2) * TI; e += NTHREADS) {
+            if (e < TJ * (TI + 2)) {
+                int r = e / (TI + 2), c = e % (TI + 2) - 1;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    R pl, mn;
+                    face_states<R, LIM>(W_at(v, r, c - 1), W_at(v, r, c), W_at(v, r, c + 1), c1, c2, half_eps, pl, mn);
+                    sPi[v * PIV + r * PIP + (c + 1)] = pl;
+                    sPi[PIS + v * PIV + r * PIP + (c + 1)] = mn;
+                }
+            } else {
+                int e2 = e - TJ * (TI + 2);
+                int r = e2 / TI - 1, c = e2 % TI;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    R pl, mn;
+                    face_states<R, LIM>(W_at(v, r - 1, c), W_at(v, r, c), W_at(v, r + 1, c), c1, c2, half_eps, pl, mn);
+                    sPj[v * PJV + (r + 1) * PJP + c] = pl;
+                    sPj[PJS + v * PJV + (r + 1) * PJP + c] = mn;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- P2: Roe flux of every i-face and j-face of the tile, once each
+        const long long kpl = (long long)k * p.ml.mplane;
+        for (int e = t; e < TJ * (TI + 1) + (TJ + 1) * TI; e += NTHREADS) {
+            R Lf[NV], Rf[NV], F[NV];
+            int fam, fi, fj;
+            R *dst;
+            if (e < TJ * (TI + 1)) {
+                int r = e / (TI + 1), c = e % (TI + 1);   // face between cells c-1 and c of row r
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    Lf[v] = sPi[v * PIV + r * PIP + c];
+                    Rf[v] = sPi[PIS + v * PIV + r * PIP + (c + 1)];
+                }
+                fam = 0;
+                fi = i0 + c;
+                fj = j0 + r;
+                dst = sFi + r * FIP + c;
+            } else {
+                int e2 = e - TJ * (TI + 1);
+                int r = e2 / TI, c = e2 % TI;              // face between rows r-1 and r of column c
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    Lf[v] = sPj[v * PJV + r * PJP + c];
+                    Rf[v] = sPj[PJS + v * PJV + (r + 1) * PJP + c];
+                }
+                fam = 1;
+                fi = i0 + c;
+                fj = j0 + r;
+                dst = sFj + r * FJP + c;
+            }
+            bool valid = fam == 0 ? (fi <= p.ni && fj < p.nj) : (fi < p.ni && fj <= p.nj);
+            R nx = R(1), ny = R(0), nz = R(0), A = R(0);
+            if (valid) {
+                long long m = kpl + (long long)fj * p.ml.mpitch + fi;
+                nx = p.fm.n[fam][0][m];
+                ny = p.fm.n[fam][1][m];
+                nz = p.fm.n[fam][2][m];
+                A = p.fm.n[fam][3][m];
+            }
+            face_flux(Lf, Rf, nx, ny, nz, A, gm1, kg, p.fix, cons, F);
+            const int vstride = fam == 0 ? FIV : FJV;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) dst[v * vstride] = F[v];
+        }
+        R Fkp[NV], Ppn[NV];
+        if (!TWO_D) {
+            // face k+1/2 of the own column: left = plus state of plane k,
+            // right = minus state of plane k+1
+            R Rk[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) face_states<R, LIM>(Wc[v], W1[v], W2[v], c1, c2, half_eps, Ppn[v], Rk[v]);
+            long long fk = (long long)(k + 1) * p.ml.mplane + (long long)min(cj, p.nj - 1) * p.ml.mpitch +
+                           min(ci, p.ni - 1);
+            face_flux(Pp, Rk, p.fm.n[2][0][fk], p.fm.n[2][1][fk], p.fm.n[2][2][fk], p.fm.n[2][3][fk], gm1, kg, p.fix,
+                      cons, Fkp);
+        }
+        __syncthreads();
+
+        // ---- P3: residual, update, norms
+        if (col_valid) {
+            const long long cell = p.L.off + (long long)k * p.L.sk + (long long)cj * p.L.sj + ci;
+            const long long mc = kpl + (long long)cj * p.ml.mpitch + ci;
+            const long long rc = ((long long)k * p.nj + cj) * p.ni + ci;
+            const long long nint = (long long)p.ni * p.nj * p.nk;
+            const double ivol = p.cm.ivol[mc];
+            const double vol = p.cm.vol[mc];
+            const double coef = -p.gdt * dt * ivol;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                R rr = (sFi[v * FIV + tj * FIP + ti + 1] - sFi[v * FIV + tj * FIP + ti]) +
+                       (sFj[v * FJV + (tj + 1) * FJP + ti] - sFj[v * FJV + tj * FJP + ti]);
+                if (!TWO_D) rr += Fkp[v] - Fkm[v];
+                double r = (double)rr;
+                if (p.src) r -= p.src[v * nint + rc];
+                const double uin = p.in[cell + v * p.L.sv];
+                if (update) {
+                    double val = p.beta * uin + coef * r;
+                    if (p.un) val += p.alpha * p.un[cell + v * p.L.sv];
+                    p.out[cell + v * p.L.sv] = val;
+                } else {
+                    p.Rout[v * nint + rc] = r;
+                }
+                if (p.partials) {
+                    nsq[v] += r * r;
+                    nmax[v] = fmax(nmax[v], fabs(r));
+                    ncons[v] += vol * uin;
+                }
+            }
+        }
+        if (!TWO_D) {
+            double q[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                Fkm[v] = Fkp[v];
+                Pp[v] = Ppn[v];
+                Wc[v] = W1[v];
+                W1[v] = W2[v];
+                q[v] = pre[v];
+            }
+            to_recon(q, gm1, cons, col_valid && k + 3 < p.nk, p.err, W2);
+        }
+    }
+
+    // ---- FP64 norm partials of this CTA, fixed-order reduction
+    if (p.partials) {
+        const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double a = nsq[v], b = nmax[v], c = ncons[v];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(0xffffffffu, a, o);
+                b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+                c += __shfl_down_sync(0xffffffffu, c, o);
+            }
+            if (lane == 0) {
+                sRed[(0 * NV + v) * (NTHREADS / 32) + warp] = a;
+                sRed[(1 * NV + v) * (NTHREADS / 32) + warp] = b;
+                sRed[(2 * NV + v) * (NTHREADS / 32) + warp] = c;
+            }
+        }
+        __syncthreads();
+        if (t < 3 * NV) {
+            int kind = t / NV;
+            double acc = 0.0;
+            for (int w = 0; w < NTHREADS / 32; ++w) {
+                double x = sRed[t * (NTHREADS / 32) + w];
+                acc = kind == 1 ? fmax(acc, x) : acc + x;
+            }
+            p.partials[(long long)blockIdx.x * 3 * NV + t] = acc;
+        }
+    }
+}
+
+template <typename R>
+cudaError_t launch_stencil_t(const StencilParams<R> &p, int limiter, bool two_d, cudaStream_t s)
+{
+    const size_t smem = SmemLayout<R>::bytes;
+    const unsigned grid = (unsigned)((long long)p.tiles_i * p.tiles_j * (two_d ? 1 : p.nchunks));
+    void (*fn)(const StencilParams<R>) = nullptr;
+#define SENSEI_PICK(L)                                                                                  \
+    fn = two_d ? stencil_kernel<R, L, true> : stencil_kernel<R, L, false>;
+    switch (limiter) {
+    case SENSEI_LIM_NONE: SENSEI_PICK(SENSEI_LIM_NONE); break;
+    case SENSEI_LIM_MINMOD: SENSEI_PICK(SENSEI_LIM_MINMOD); break;
+    default: SENSEI_PICK(SENSEI_LIM_VANLEER); break;
+    }
+#undef SENSEI_PICK
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, NTHREADS, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace sensei

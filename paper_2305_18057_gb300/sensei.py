@@ -1,0 +1,247 @@
+"""Thin ctypes binding of the C ABI in ``include/sensei.h`` (``libsensei.so``).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of ``csrc/``.  PyTorch supplies device memory and streams.  There is
+no fallback: if the library cannot be loaded, every entry point raises.
+
+Functions with the C names (``sensei_create_grid`` ...) take raw integers
+(device addresses) and ctypes arrays, exactly like the C calls.  ``Grid`` is
+a convenience owner of a grid, its workspace tensor and state tensors laid out
+as ``sensei_state_layout`` says.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsensei.so")
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_STATE = range(7)
+FP64, FP32_FLUX, FP32_STORE = 0, 1, 2
+BC_PERIODIC, BC_INFLOW, BC_EXTRAPOLATE, BC_SLIP_WALL, BC_INTERFACE = range(5)
+RK2_SSP, RK3_SSP, RK4_SSP2 = range(3)
+LIM_NONE, LIM_MINMOD, LIM_VANLEER = range(3)
+NV = 5
+
+# every symbol include/sensei.h declares
+EXPORTS = ("sensei_workspace_size", "sensei_create_grid", "sensei_destroy_grid", "sensei_state_layout",
+           "sensei_set_bc", "sensei_fill_ghosts", "sensei_residual", "sensei_rk_step", "sensei_norms",
+           "sensei_profile_enable", "sensei_profile_read", "sensei_last_error")
+
+
+class BlockDesc(C.Structure):
+    _fields_ = [("ni", C.c_int), ("nj", C.c_int), ("nk", C.c_int)]
+
+
+class Scheme(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("limiter", C.c_int), ("kappa", C.c_double), ("eps", C.c_double),
+                ("entropy_fix", C.c_double), ("precision", C.c_int), ("reconstruct_conserved", C.c_int)]
+
+
+class Layout(C.Structure):
+    _fields_ = [("stride_j", C.c_longlong), ("stride_k", C.c_longlong), ("stride_var", C.c_longlong),
+                ("offset", C.c_longlong), ("elems", C.c_longlong), ("ghost_i", C.c_int), ("ghost_j", C.c_int),
+                ("ghost_k", C.c_int), ("elem_bytes", C.c_int)]
+
+
+class SenseiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"sensei status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsensei.so (built by ``paper_2305_18057_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2305_18057_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    L = C.CDLL(path)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    L.sensei_workspace_size.argtypes = [C.POINTER(BlockDesc), C.c_int, C.POINTER(Scheme), C.POINTER(C.c_size_t)]
+    L.sensei_create_grid.argtypes = [C.POINTER(BlockDesc), C.c_int, C.POINTER(vp), C.POINTER(Scheme), vp,
+                                     C.c_size_t, vp, C.POINTER(vp)]
+    L.sensei_destroy_grid.argtypes = [vp]
+    L.sensei_state_layout.argtypes = [vp, C.c_int, C.POINTER(Layout)]
+    L.sensei_set_bc.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, C.c_int, C.c_int, C.c_int]
+    L.sensei_fill_ghosts.argtypes = [vp, C.POINTER(vp), vp]
+    L.sensei_residual.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]
+    L.sensei_rk_step.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_double, C.c_double, vp, vp]
+    L.sensei_norms.argtypes = [vp, dp, dp, dp, vp]
+    L.sensei_profile_enable.argtypes = [vp, C.c_int]
+    L.sensei_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
+    L.sensei_last_error.argtypes = []
+    L.sensei_last_error.restype = C.c_char_p
+    for name in EXPORTS[:-1]:
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != OK:
+        raise SenseiError(status, load().sensei_last_error().decode())
+    return status
+
+
+def _ptrs(addrs):
+    arr = (C.c_void_p * len(addrs))()
+    for n, a in enumerate(addrs):
+        arr[n] = a
+    return arr
+
+
+# ------------------------------------------------------- the C entry points --
+
+def sensei_workspace_size(blocks, scheme) -> int:
+    b = (BlockDesc * len(blocks))(*[BlockDesc(*d) for d in blocks])
+    n = C.c_size_t()
+    _check(load().sensei_workspace_size(b, len(blocks), C.byref(scheme), C.byref(n)))
+    return n.value
+
+
+def sensei_create_grid(blocks, node_ptrs, scheme, workspace_ptr, workspace_bytes, stream_ptr):
+    b = (BlockDesc * len(blocks))(*[BlockDesc(*d) for d in blocks])
+    out = C.c_void_p()
+    _check(load().sensei_create_grid(b, len(blocks), _ptrs(node_ptrs), C.byref(scheme), workspace_ptr,
+                                     workspace_bytes, stream_ptr, C.byref(out)))
+    return out.value
+
+
+def sensei_destroy_grid(grid):
+    return _check(load().sensei_destroy_grid(grid))
+
+
+def sensei_state_layout(grid, block) -> Layout:
+    lay = Layout()
+    _check(load().sensei_state_layout(grid, block, C.byref(lay)))
+    return lay
+
+
+def sensei_set_bc(grid, block, face, bc_type, prim=None, nbr_block=-1, nbr_face=-1, orientation=0):
+    p = (C.c_double * 5)(*prim) if prim is not None else None
+    return _check(load().sensei_set_bc(grid, block, face, bc_type, p, nbr_block, nbr_face, orientation))
+
+
+def sensei_fill_ghosts(grid, U_ptrs, stream_ptr):
+    return _check(load().sensei_fill_ghosts(grid, _ptrs(U_ptrs), stream_ptr))
+
+
+def sensei_residual(grid, U_ptrs, R_ptrs, src_ptrs, stream_ptr):
+    s = _ptrs(src_ptrs) if src_ptrs is not None else None
+    return _check(load().sensei_residual(grid, _ptrs(U_ptrs), _ptrs(R_ptrs), s, stream_ptr))
+
+
+def sensei_rk_step(grid, U_ptrs, rk, cfl, dt, dt_used_ptr, stream_ptr):
+    return _check(load().sensei_rk_step(grid, _ptrs(U_ptrs), rk, cfl, dt, dt_used_ptr, stream_ptr))
+
+
+def sensei_norms(grid, stream_ptr, check=True):
+    l2, linf, cons = (C.c_double * 5)(), (C.c_double * 5)(), (C.c_double * 5)()
+    st = load().sensei_norms(grid, l2, linf, cons, stream_ptr)
+    if check:
+        _check(st)
+    return st, np.array(l2[:]), np.array(linf[:]), np.array(cons[:])
+
+
+def sensei_profile_enable(grid, enable):
+    return _check(load().sensei_profile_enable(grid, int(enable)))
+
+
+def sensei_profile_read(grid, reset=True):
+    """(stencil_ms, stencil_launches, kernel_launches) since the last reset."""
+    ms, ns, nk = C.c_double(), C.c_longlong(), C.c_longlong()
+    _check(load().sensei_profile_read(grid, C.byref(ms), C.byref(ns), C.byref(nk), int(reset)))
+    return ms.value, ns.value, nk.value
+
+
+def sensei_last_error() -> str:
+    return load().sensei_last_error().decode()
+
+
+# ------------------------------------------------------------ convenience --
+
+class Grid:
+    """A grid on the current CUDA device with its workspace and state tensors.
+
+    blocks: [(ni, nj, nk)], nodes: [(3, nk+1, nj+1, ni+1) float64 array or
+    tensor].  ``scheme`` keys: gamma, limiter, kappa, eps, entropy_fix,
+    precision, reconstruct_conserved.
+    """
+
+    def __init__(self, blocks, nodes, stream=None, **scheme):
+        import torch
+        self.torch = torch
+        self.blocks = [tuple(int(v) for v in d) for d in blocks]
+        self.scheme = Scheme(scheme.get("gamma", 1.4), scheme.get("limiter", LIM_VANLEER),
+                             scheme.get("kappa", 1.0 / 3.0), scheme.get("eps", 1.0), scheme.get("entropy_fix", 0.1),
+                             scheme.get("precision", FP64), int(scheme.get("reconstruct_conserved", 0)))
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ws_bytes = sensei_workspace_size(self.blocks, self.scheme)
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.dev)
+        self._nodes = [torch.as_tensor(X, dtype=torch.float64).to(self.dev).contiguous() for X in nodes]
+        self.handle = sensei_create_grid(self.blocks, [X.data_ptr() for X in self._nodes], self.scheme,
+                                         self.workspace.data_ptr(), self.ws_bytes, self.stream.cuda_stream)
+        self.layouts = [sensei_state_layout(self.handle, b) for b in range(len(self.blocks))]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sensei_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def sptr(self):
+        return self.stream.cuda_stream
+
+    def set_bc(self, block, face, bc_type, prim=None, nbr=-1, nbr_face=-1):
+        sensei_set_bc(self.handle, block, face, bc_type, prim, nbr, nbr_face, 0)
+
+    def new_state(self, block):
+        return self.torch.zeros(self.layouts[block].elems, dtype=self.torch.float64, device=self.dev)
+
+    def interior_view(self, U, block):
+        """(5, nk, nj, ni) view of a state tensor's interior cells."""
+        ni, nj, nk = self.blocks[block]
+        L = self.layouts[block]
+        return U.as_strided((5, nk, nj, ni), (L.stride_var, L.stride_k, L.stride_j, 1), L.offset)
+
+    def upload(self, U, block, interior):
+        self.interior_view(U, block).copy_(self.torch.as_tensor(interior, dtype=self.torch.float64))
+
+    def download(self, U, block):
+        return self.interior_view(U, block).cpu().numpy().copy()
+
+    def fill_ghosts(self, Us):
+        sensei_fill_ghosts(self.handle, [U.data_ptr() for U in Us], self.sptr)
+
+    def residual(self, Us, Rs, srcs=None):
+        sensei_residual(self.handle, [U.data_ptr() for U in Us], [R.data_ptr() for R in Rs],
+                        [s.data_ptr() for s in srcs] if srcs is not None else None, self.sptr)
+
+    def rk_step(self, Us, rk=RK3_SSP, cfl=0.5, dt=0.0, dt_used=None):
+        sensei_rk_step(self.handle, [U.data_ptr() for U in Us], rk, cfl, dt,
+                       dt_used.data_ptr() if dt_used is not None else None, self.sptr)
+
+    def norms(self, check=True):
+        return sensei_norms(self.handle, self.sptr, check=check)
+
+    def profile(self, enable=True):
+        sensei_profile_enable(self.handle, enable)
+
+    def profile_read(self, reset=True):
+        return sensei_profile_read(self.handle, reset)

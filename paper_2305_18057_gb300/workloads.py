@@ -98,10 +98,23 @@ def conserved(rho, u, v, w, p, gamma=GAMMA):
     return Q
 
 
-def uniform_state(dims, prim, gamma=GAMMA):
+def uniform_state(dims, prim, gamma=GAMMA, perturb=0.0, seed=0):
+    """Conserved state of a uniform primitive state; with perturb > 0, rho and
+    p are multiplied by 1 + perturb * U(-1, 1) and every velocity component
+    gets perturb * |u| * U(-1, 1) (seeded), cell by cell."""
     ni, nj, nk = dims
     ones = np.ones((nk, nj, ni))
-    return conserved(prim[0] * ones, prim[1] * ones, prim[2] * ones, prim[3] * ones, prim[4] * ones, gamma)
+    rho, u, v, w, p = (c * ones for c in prim)
+    if perturb > 0.0:
+        rng = np.random.default_rng(seed)
+        speed = math.sqrt(prim[1] ** 2 + prim[2] ** 2 + prim[3] ** 2)
+        rho = rho * (1.0 + perturb * rng.uniform(-1, 1, ones.shape))
+        p = p * (1.0 + perturb * rng.uniform(-1, 1, ones.shape))
+        u = u + perturb * speed * rng.uniform(-1, 1, ones.shape)
+        v = v + perturb * speed * rng.uniform(-1, 1, ones.shape)
+        if nk > 1:
+            w = w + perturb * speed * rng.uniform(-1, 1, ones.shape)
+    return conserved(rho, u, v, w, p, gamma)
 
 
 def cell_centres(X):
@@ -200,7 +213,7 @@ def bump(x, y, centre, amp=0.1, width=0.1):
     return amp * np.exp(-(dx * dx + dy * dy) / (width * width))
 
 
-def ramp_2d(ni=1024, nj=512, ratio=1.02, angle_deg=10.0, steps=500):
+def ramp_2d(ni=1024, nj=512, ratio=1.02, angle_deg=10.0, steps=500, perturb=0.0, seed=2308):
     """2D supersonic compression ramp (inlet-like): x in [0, 2], 10-deg ramp
     from x = 0.5, top wall y = 1, geometric wall-normal stretching `ratio`;
     the paper's inflow state (Mach 4, 12270 Pa, 217 K) enters at imin and
@@ -209,7 +222,7 @@ def ramp_2d(ni=1024, nj=512, ratio=1.02, angle_deg=10.0, steps=500):
     RK3."""
     X = ramp_nodes(ni, nj, 1, ratio=ratio, angle_deg=angle_deg)
     prim = inlet_inflow()
-    U0 = uniform_state((ni, nj, 1), prim)
+    U0 = uniform_state((ni, nj, 1), prim, perturb=perturb, seed=seed)
     bcs = [BC(INFLOW, prim), BC(EXTRAPOLATE), BC(SLIP_WALL), BC(INFLOW, prim), BC(PERIODIC), BC(PERIODIC)]
     return Workload("ramp2d", [(ni, nj, 1)], [X], [U0], [bcs], limiter="vanleer", rk="rk3",
                     cfl=0.5, steps=steps)
@@ -238,7 +251,7 @@ def periodic_3d(n=256, seed=2307, mach=2.5, limiter="vanleer", steps=100, nj=Non
                     rk="rk3", cfl=0.5, steps=steps)
 
 
-def ramp_3d(n=512, ratio=1.005, angle_deg=8.0, steps=50, ni=None, nj=None, nk=None):
+def ramp_3d(n=512, ratio=1.005, angle_deg=8.0, steps=50, ni=None, nj=None, nk=None, perturb=0.0, seed=2310):
     """3D Mach-4 compression ramp, 8-deg ramp extruded in k (periodic in k),
     wall-normal geometric stretching `ratio`, the paper's inflow state."""
     ni = n if ni is None else ni
@@ -246,14 +259,14 @@ def ramp_3d(n=512, ratio=1.005, angle_deg=8.0, steps=50, ni=None, nj=None, nk=No
     nk = n if nk is None else nk
     X = ramp_nodes(ni, nj, nk, ratio=ratio, angle_deg=angle_deg, depth=1.0)
     prim = inlet_inflow()
-    U0 = uniform_state((ni, nj, nk), prim)
+    U0 = uniform_state((ni, nj, nk), prim, perturb=perturb, seed=seed)
     bcs = [BC(INFLOW, prim), BC(EXTRAPOLATE), BC(SLIP_WALL), BC(INFLOW, prim), BC(PERIODIC), BC(PERIODIC)]
     return Workload("ramp3d", [(ni, nj, nk)], [X], [U0], [bcs], limiter="vanleer", rk="rk3",
                     cfl=0.5, steps=steps)
 
 
 def lattice_3d(sizes=(32, 48, 64, 96, 128), nblk=(4, 4, 4), seed=2309, mach=3.0, ratio=1.01,
-               angle_deg=10.0, steps=20):
+               angle_deg=10.0, steps=20, perturb=0.0):
     """Batched multiblock 3D: a global ramp-like curvilinear grid cut into a
     nblk[0] x nblk[1] x nblk[2] lattice; block (a, b, c) has (X_a, Y_b, Z_c)
     cells with X, Y, Z seeded draws from `sizes`.  Faces match point to point
@@ -281,7 +294,7 @@ def lattice_3d(sizes=(32, 48, 64, 96, 128), nblk=(4, 4, 4), seed=2309, mach=3.0,
                 dims.append((ni, nj, nk))
                 nodes.append(np.ascontiguousarray(
                     Xg[:, ko[c]:ko[c + 1] + 1, jo[b]:jo[b + 1] + 1, io[a]:io[a + 1] + 1]))
-                U0.append(uniform_state((ni, nj, nk), prim))
+                U0.append(uniform_state((ni, nj, nk), prim, perturb=perturb, seed=seed + len(U0)))
                 f = [None] * 6
                 f[IMIN] = BC(INTERFACE, None, bid(a - 1, b, c), IMAX) if a > 0 else BC(INFLOW, prim)
                 f[IMAX] = BC(INTERFACE, None, bid(a + 1, b, c), IMIN) if a < A - 1 else BC(EXTRAPOLATE)

@@ -1,0 +1,141 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle,
+element by element, on seeded inputs spanning several tiles and ragged tails.
+
+Tolerances: one residual 1e-11 relative (per variable, scaled by the largest
+oracle value of that variable); the state after 100 steps 1e-9; dt 1e-14;
+the conservation sums 1e-13."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import gpu_grid, gpu_states, oracle_grid, oracle_states, per_var_rel
+from paper_2305_18057_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+RK = {"rk2": 0, "rk3": 1, "rk4": 2}
+
+CASES = {
+    # i: 37 = 32 + 5 (ragged i tile), j: 19 = 8 + 8 + 3, k: 11
+    "periodic3d_odd": lambda: wl.periodic_3d(n=37, nj=19, nk=11, seed=3),
+    # inflow, extrapolation, slip wall on the ramp, periodic k
+    "ramp3d": lambda: wl.ramp_3d(ni=40, nj=20, nk=9, ratio=1.05, perturb=0.05),
+    "advection2d": lambda: wl.advection_2d(n=48),
+    "ramp2d": lambda: wl.ramp_2d(ni=70, nj=33, ratio=1.03, perturb=0.05),
+    # 8 uneven blocks, interface ghost exchange in every direction
+    "lattice": lambda: wl.lattice_3d(sizes=(6, 9, 13), nblk=(2, 2, 2), seed=4, perturb=0.05),
+}
+
+
+def _residuals(w, limiter=None, kappa=None, recon=False, fix=None):
+    og = oracle_grid(w, limiter=limiter, kappa=kappa, recon_conserved=recon, fix=fix)
+    Ro = og.residual(oracle_states(og, w))
+    g = gpu_grid(w, limiter=limiter, kappa=kappa, recon_conserved=recon, fix=fix)
+    Us = gpu_states(g, w)
+    Rs = [torch.empty((5, nk, nj, ni), dtype=torch.float64, device=Us[0].device) for ni, nj, nk in w.dims]
+    g.residual(Us, Rs)
+    torch.cuda.synchronize()
+    return [R.cpu().numpy() for R in Rs], Ro, g, og, Us
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("limiter", ["none", "minmod", "vanleer"])
+def test_residual_parity(case, limiter):
+    w = CASES[case]()
+    Rg, Ro, *_ = _residuals(w, limiter=limiter)
+    for b in range(len(w.dims)):
+        assert per_var_rel(Rg[b], Ro[b]) < 1e-11, (case, limiter, b)
+
+
+@pytest.mark.parametrize("case", ["periodic3d_odd", "ramp2d"])
+def test_residual_parity_options(case):
+    w = CASES[case]()
+    for kw in (dict(limiter="none", kappa=-1.0), dict(limiter="minmod", recon=True), dict(limiter="vanleer", fix=0.0),
+               dict(limiter="vanleer", fix=0.3, recon=True)):
+        Rg, Ro, *_ = _residuals(w, **kw)
+        assert per_var_rel(Rg[0], Ro[0]) < 1e-11, kw
+
+
+def test_residual_with_source_and_norms():
+    w = CASES["periodic3d_odd"]()
+    ni, nj, nk = w.dims[0]
+    rng = np.random.default_rng(0)
+    src = rng.normal(size=(5, nk, nj, ni)) * 1e-4
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    Ro = og.residual(Uo, src=[np.ascontiguousarray(src)])
+    g = gpu_grid(w)
+    Us = gpu_states(g, w)
+    R = torch.empty((5, nk, nj, ni), dtype=torch.float64, device=Us[0].device)
+    g.residual(Us, [R], [torch.as_tensor(src, device=R.device)])
+    st, l2, linf, cons = g.norms()
+    assert per_var_rel(R.cpu().numpy(), Ro[0]) < 1e-11
+    ol2, olinf, ocons = og.norms(Ro, Uo)
+    np.testing.assert_allclose(l2, ol2, rtol=1e-11)
+    np.testing.assert_allclose(linf, olinf, rtol=1e-11)
+    np.testing.assert_allclose(cons, ocons, rtol=1e-13, atol=1e-13 * np.abs(ocons).max())
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_dt_parity(case):
+    w = CASES[case]()
+    og = oracle_grid(w)
+    dto = 0.5 * og.dt_min(oracle_states(og, w))
+    g = gpu_grid(w)
+    Us = gpu_states(g, w)
+    dt_used = torch.zeros(1, dtype=torch.float64, device=Us[0].device)
+    g.rk_step(Us, RK["rk3"], cfl=0.5, dt_used=dt_used)
+    assert abs(dt_used.item() - dto) <= 1e-14 * dto
+
+
+@pytest.mark.parametrize("case,rk,steps", [("periodic3d_small", "rk3", 100), ("advection2d", "rk3", 100),
+                                           ("ramp2d", "rk2", 100), ("lattice", "rk4", 100),
+                                           ("ramp3d", "rk3", 30)])
+def test_state_after_many_steps(case, rk, steps):
+    w = wl.periodic_3d(n=24, nj=16, nk=12, seed=8) if case == "periodic3d_small" else CASES[case]()
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    g = gpu_grid(w)
+    Us = gpu_states(g, w)
+    dt_used = torch.zeros(1, dtype=torch.float64, device=Us[0].device)
+    for n in range(steps):
+        g.rk_step(Us, RK[rk], cfl=0.5, dt_used=dt_used)
+        # same dt on both sides: the oracle takes the GPU's dt explicitly
+        # (dt itself is checked by test_dt_parity)
+        og.rk_step(Uo, RK[rk], dt=dt_used.item())
+    torch.cuda.synchronize()
+    for b in range(len(w.dims)):
+        assert per_var_rel(g.download(Us[b], b), og.interior(Uo[b], b)) < 1e-9, (case, b)
+
+
+def test_norms_of_step_match_oracle():
+    w = CASES["ramp3d"]()
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    g = gpu_grid(w)
+    Us = gpu_states(g, w)
+    g.rk_step(Us, RK["rk3"], dt=1e-7)
+    st, l2, linf, cons = g.norms()
+    _, (ol2, olinf, ocons) = og.rk_step(Uo, RK["rk3"], dt=1e-7)
+    np.testing.assert_allclose(l2, ol2, rtol=1e-11)
+    np.testing.assert_allclose(linf, olinf, rtol=1e-11)
+    np.testing.assert_allclose(cons, ocons, rtol=1e-13)
+
+
+def test_nonphysical_state_is_reported():
+    from paper_2305_18057_gb300 import sensei
+    w = CASES["periodic3d_odd"]()
+    U0 = [w.U0[0].copy()]
+    U0[0][4, 3, 5, 7] = 0.0          # rho e_t = 0: negative pressure in one cell
+    g = gpu_grid(w)
+    Us = gpu_states(g, w, U0)
+    g.rk_step(Us, RK["rk3"], dt=1e-6)
+    st, *_ = g.norms(check=False)
+    assert st == sensei.ERR_NONPHYSICAL
+    # the flag is cleared once reported
+    g.upload(Us[0], 0, w.U0[0])
+    g.rk_step(Us, RK["rk3"], dt=1e-6)
+    st, *_ = g.norms(check=False)
+    assert st == sensei.OK
