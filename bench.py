@@ -150,18 +150,18 @@ class ClockSampler:
 
 # ------------------------------------------------------------- workloads --
 
-def make_workload(name, small=False):
+def make_workload(name, n=None):
     from paper_2305_18057_gb300 import workloads as wl
     if name == "c3":
-        return wl.periodic_3d(n=64 if small else 256)
+        return wl.periodic_3d(n=n or 256)
     if name == "c1":
         return wl.advection_2d(n=128)
     if name == "c2":
         return wl.ramp_2d(ni=1024, nj=512)
     if name == "c4":
-        return wl.lattice_3d() if not small else wl.lattice_3d(sizes=(8, 12, 16))
+        return wl.lattice_3d()
     if name == "c5":
-        return wl.ramp_3d(n=128 if small else 512)
+        return wl.ramp_3d(n=n or 512)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -281,6 +281,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="grid size override (c3, c5): small profiling cases")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -301,7 +302,7 @@ def main():
     torch.cuda.set_device(local)
     sensei.load()
 
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.n)
     two_d = all(d[2] == 1 for d in w.dims)
     cells = w.cells
     rk = sensei.RK3_SSP
