@@ -204,6 +204,25 @@ sensei_status sensei_profile_enable(sensei_grid *grid, int enable);
 sensei_status sensei_profile_read(sensei_grid *grid, double *stencil_ms, long long *stencil_launches,
                                   long long *kernel_launches, int reset);
 
+/* Residual norms that allocate nothing.  The paper has no counterpart: this
+ * exists for callers that cannot allocate device memory, e.g. a solver
+ * embedded in an application whose memory pool already owns the device, or
+ * a monitor inside a time-critical loop that must not risk an allocation.
+ * It needs no grid and no workspace.  R is a dense device array
+ * R[5][nk][nj][ni] (the layout sensei_residual writes); l2 and linf (host,
+ * 5 doubles each, either may be NULL) receive sqrt(sum R_q^2 / N) and
+ * max |R_q| over the N = ni*nj*nk cells.  Synchronises `stream`.
+ * Scratch: a fixed 164 KB array in the library's own device memory, held by
+ * every GPU that loads the library until the process exits; N above
+ * 8,388,608 cells is rejected with SENSEI_ERR_INVALID_ARG.  The first call on
+ * a device looks up that array's address (once per device, with the device
+ * current); make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents (each call overwrites every
+ * slot it reads), so calls that overlap on the GPU, from different streams
+ * or threads, race: serialise them. */
+sensei_status sensei_residual_norms_noalloc(const double *R, int ni, int nj, int nk, double *l2, double *linf,
+                                            sensei_stream stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *sensei_last_error(void);
 

@@ -179,6 +179,15 @@ struct Device {
 
 }  // namespace
 
+sensei_status sensei::fail_status(sensei_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
 struct sensei_grid {
     int device;
     sensei_scheme scheme;

@@ -121,6 +121,9 @@ cudaError_t launch_dt(int ni, int nj, int nk, const StateLayout &L, const double
                       cudaStream_t s);
 cudaError_t launch_set_scalar(double *slot, double v, cudaStream_t s);
 cudaError_t launch_scale_copy(double *dst, const double *src, double scale, cudaStream_t s);
+// Record the thread-local message returned by sensei_last_error (api.cu).
+sensei_status fail_status(sensei_status st, const char *fmt, ...);
+
 cudaError_t launch_norms_finalize(const double *partials, int nparts, long long ncells, double *out15,
                                   cudaStream_t s);
 

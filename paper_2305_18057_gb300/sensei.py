@@ -29,7 +29,7 @@ NV = 5
 # every symbol include/sensei.h declares
 EXPORTS = ("sensei_workspace_size", "sensei_create_grid", "sensei_destroy_grid", "sensei_state_layout",
            "sensei_set_bc", "sensei_fill_ghosts", "sensei_residual", "sensei_rk_step", "sensei_norms",
-           "sensei_profile_enable", "sensei_profile_read", "sensei_last_error")
+           "sensei_profile_enable", "sensei_profile_read", "sensei_residual_norms_noalloc", "sensei_last_error")
 
 
 class BlockDesc(C.Structure):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.sensei_norms.argtypes = [vp, dp, dp, dp, vp]
     L.sensei_profile_enable.argtypes = [vp, C.c_int]
     L.sensei_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
+    L.sensei_residual_norms_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, dp, vp]
     L.sensei_last_error.argtypes = []
     L.sensei_last_error.restype = C.c_char_p
     for name in EXPORTS[:-1]:
@@ -161,6 +162,15 @@ def sensei_profile_read(grid, reset=True):
     ms, ns, nk = C.c_double(), C.c_longlong(), C.c_longlong()
     _check(load().sensei_profile_read(grid, C.byref(ms), C.byref(ns), C.byref(nk), int(reset)))
     return ms.value, ns.value, nk.value
+
+
+def sensei_residual_norms_noalloc(R_ptr, ni, nj, nk, stream_ptr):
+    """L2 and max norms of a dense residual R[5][nk][nj][ni] without any
+    device allocation (for callers whose device memory is not theirs to
+    allocate); returns (l2, linf)."""
+    l2, linf = (C.c_double * 5)(), (C.c_double * 5)()
+    _check(load().sensei_residual_norms_noalloc(R_ptr, ni, nj, nk, l2, linf, stream_ptr))
+    return np.array(l2[:]), np.array(linf[:])
 
 
 def sensei_last_error() -> str:
