@@ -39,18 +39,80 @@ struct SmemLayout {
     static constexpr size_t bytes = sizeof(R) * (size_t)elems + sizeof(double) * red_doubles + 16;
 };
 
+// Reciprocal and reciprocal square root of positive normal numbers by
+// Newton-Raphson refinement of the hardware approximations.  FP64: the PTX
+// rcp.approx.ftz.f64 / rsqrt.approx.ftz.f64 seeds carry 20 correct bits
+// (measured on sm_103a); each Newton step doubles that: STEPS = 1 gives
+// ~1e-12 relative error (used where the value only scales the Roe
+// dissipation or a limited slope), STEPS = 2 reaches the correctly rounded
+// value (used where it enters the state or the central flux).  The
+// reciprocal step is r' = r + r (1 - d r); the rsqrt step
+// y' = y + (y/2) (1 - x y^2).  FP32: the single-precision intrinsics.
+template <int STEPS>
+__device__ __forceinline__ double rcp_nr(double d)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+#pragma unroll
+    for (int n = 0; n < STEPS; ++n) {
+        double e = fma(-d, r, 1.0);
+        r = fma(r, e, r);
+    }
+    return r;
+}
+
+template <int STEPS>
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+#pragma unroll
+    for (int n = 0; n < STEPS; ++n) {
+        double e = fma(-(x * y), y, 1.0);
+        y = fma(0.5 * y, e, y);
+    }
+    return y;
+}
+
+template <typename R, int STEPS>
+__device__ __forceinline__ R rcp_t(R x);
+template <>
+__device__ __forceinline__ double rcp_t<double, 1>(double x) { return rcp_nr<1>(x); }
+template <>
+__device__ __forceinline__ double rcp_t<double, 2>(double x) { return rcp_nr<2>(x); }
+template <>
+__device__ __forceinline__ float rcp_t<float, 1>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ float rcp_t<float, 2>(float x) { return __frcp_rn(x); }
+
 template <typename R>
-__device__ __forceinline__ R rsqrt_t(R x);
+__device__ __forceinline__ R rsqrt1_t(R x);
 template <>
-__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+__device__ __forceinline__ double rsqrt1_t<double>(double x) { return rsqrt_nr<1>(x); }
 template <>
-__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float rsqrt1_t<float>(float x) { return rsqrtf(x); }
+
+// x > 0 (nonzero, not NaN) and the sign of x, from the bit pattern (integer
+// pipe, keeps compares off the FP64 pipe)
+__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool positive(float x) { return __float_as_int(x) > 0; }
+__device__ __forceinline__ bool same_sign(double a, double b) { return (__double2hiint(a) ^ __double2hiint(b)) >= 0; }
+__device__ __forceinline__ bool same_sign(float a, float b) { return (__float_as_int(a) ^ __float_as_int(b)) >= 0; }
+// |a| <= |b| by the bit patterns of the magnitudes
+__device__ __forceinline__ bool abs_le(double a, double b)
+{
+    return (__double_as_longlong(a) & 0x7fffffffffffffffLL) <= (__double_as_longlong(b) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool abs_le(float a, float b)
+{
+    return (__float_as_int(a) & 0x7fffffff) <= (__float_as_int(b) & 0x7fffffff);
+}
 
 // conserved -> primitive; true if rho > 0, p > 0 and both finite
 template <typename R>
 __device__ __forceinline__ bool to_prim(const R q[NV], R gm1, R w[NV])
 {
-    R ir = R(1) / q[0];
+    R ir = rcp_t<R, 2>(q[0]);
     R u = q[1] * ir, v = q[2] * ir, ww = q[3] * ir;
     R p = gm1 * (q[4] - R(0.5) * (q[1] * u + q[2] * v + q[3] * ww));
     w[0] = q[0];
@@ -77,15 +139,20 @@ __device__ __forceinline__ void face_states(R wm, R w0, R wp, R c1, R c2, R half
         plus = w0 + (c1 * dm + c2 * dp);
         minus = w0 - (c2 * dm + c1 * dp);
     } else {
-        R s;
+        R d;
         if (LIM == SENSEI_LIM_MINMOD) {
-            R m = fmin(fabs(dm), fabs(dp));
-            s = (dm * dp > R(0)) ? copysign(m, dm) : R(0);
+            // minmod: the smaller difference if both have the same sign (a
+            // zero difference gives 0 either way); sign and magnitude tests
+            // on the bit patterns
+            R m = abs_le(dm, dp) ? dm : copysign(dp, dm);
+            d = same_sign(dm, dp) ? half_eps * m : R(0);
         } else {
+            // van Leer: 2 dm dp / (dm + dp) when dm dp > 0; the reciprocal
+            // only scales a limited slope, one Newton step suffices
             R pr = dm * dp;
-            s = (pr > R(0)) ? R(2) * pr / (dm + dp) : R(0);
+            R r = rcp_t<R, 1>(dm + dp);
+            d = positive(pr) ? (pr * r) * (R(2) * half_eps) : R(0);
         }
-        R d = half_eps * s;
         plus = w0 + d;
         minus = w0 - d;
     }
@@ -112,17 +179,22 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     c[2] = ml * vl + mr * vr + ny * psum;
     c[3] = ml * zl + mr * zr + nz * psum;
     c[4] = rhl * vnl + rhr * vnr;
-    // Roe average, weights sqrt(rho)
-    const R isl = rsqrt_t(rl), isr = rsqrt_t(rr);
-    const R sl = rl * isl, sr = rr * isr;
-    const R inv = R(1) / (sl + sr);
-    const R wL = sl * inv, wR = sr * inv;
+    // Roe average with weights sqrt(rho): with q = 1/sqrt(rl rr) and
+    // t = sqrt(rr/rl) = rr q, the weights are 1/(1+t) and t/(1+t), the
+    // averaged density sqrt(rl rr) = rl rr q and the averaged enthalpy
+    // (H_l + t H_r)/(1+t) with H_l + t H_r = (rhl rr + t rhr rl) q^2.
+    // These only enter the dissipation term: one Newton step suffices.
+    const R rlr = rl * rr;
+    const R qq = rsqrt1_t(rlr);
+    const R t = rr * qq;
+    const R wL = rcp_t<R, 1>(R(1) + t);
+    const R wR = t * wL;
     const R u = wL * ul + wR * ur, v = wL * vl + wR * vr, w = wL * zl + wR * zr;
-    const R H = (rhl * isl + rhr * isr) * inv;
-    const R rho = sl * sr;
+    const R H = wL * ((rhl * rr + (t * rhr) * rl) * (qq * qq));
+    const R rho = rlr * qq;
     const R q2 = u * u + v * v + w * w;
     const R a2 = gm1 * (H - R(0.5) * q2);
-    const R ia = rsqrt_t(a2);
+    const R ia = rsqrt1_t(a2);
     const R a = a2 * ia;
     const R ia2 = ia * ia;
     const R vn = nx * u + ny * v + nz * w;
@@ -130,8 +202,8 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     R l1 = fabs(vn - a), l3 = fabs(vn + a);
     const R l2 = fabs(vn);
     const R delta = fix * a;
-    if (l1 < delta) l1 = R(0.5) * (l1 * l1 / delta + delta);
-    if (l3 < delta) l3 = R(0.5) * (l3 * l3 / delta + delta);
+    if (l1 < delta) l1 = R(0.5) * (l1 * l1 * (ia / fix) + delta);
+    if (l3 < delta) l3 = R(0.5) * (l3 * l3 * (ia / fix) + delta);
     const R rad = rho * a * dvn;
     const R c1w = l1 * (R(0.5) * (dp - rad) * ia2);
     const R c3w = l3 * (R(0.5) * (dp + rad) * ia2);
@@ -329,25 +401,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) stencil_kernel(const StencilParam
         // ---- P1: face states, i direction (cells -1..TI of every row) and
         //      j direction (rows -1..TJ of every column)
         for (int e = t; e < TJ * (TI + 2) + (TJ + 2) * TI; e += NTHREADS) {
+            // the centre cell in sW, the stride to its neighbours along the
+            // direction, and where its two face states go
+            int wc, ws;
+            R *dst;
+            int dstride;
             if (e < TJ * (TI + 2)) {
                 int r = e / (TI + 2), c = e % (TI + 2) - 1;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    R pl, mn;
-                    face_states<R, LIM>(W_at(v, r, c - 1), W_at(v, r, c), W_at(v, r, c + 1), c1, c2, half_eps, pl, mn);
-                    sPi[v * PIV + r * PIP + (c + 1)] = pl;
-                    sPi[PIS + v * PIV + r * PIP + (c + 1)] = mn;
-                }
+                wc = (r + 2) * WP + (c + 2);
+                ws = 1;
+                dst = sPi + r * PIP + (c + 1);
+                dstride = PIV;
             } else {
                 int e2 = e - TJ * (TI + 2);
                 int r = e2 / TI - 1, c = e2 % TI;
+                wc = (r + 2) * WP + (c + 2);
+                ws = WP;
+                dst = sPj + (r + 1) * PJP + c;
+                dstride = PJV;
+            }
+            const int side = dstride == PIV ? PIS : PJS;
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    R pl, mn;
-                    face_states<R, LIM>(W_at(v, r - 1, c), W_at(v, r, c), W_at(v, r + 1, c), c1, c2, half_eps, pl, mn);
-                    sPj[v * PJV + (r + 1) * PJP + c] = pl;
-                    sPj[PJS + v * PJV + (r + 1) * PJP + c] = mn;
-                }
+            for (int v = 0; v < NV; ++v) {
+                const R *wv = sW + v * WPL + wc;
+                R pl, mn;
+                face_states<R, LIM>(wv[-ws], wv[0], wv[ws], c1, c2, half_eps, pl, mn);
+                dst[v * dstride] = pl;
+                dst[side + v * dstride] = mn;
             }
         }
         __syncthreads();
