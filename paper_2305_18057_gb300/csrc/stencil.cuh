@@ -23,6 +23,10 @@
 
 #include "sensei_internal.cuh"
 
+#ifndef SENSEI_STENCIL_MIN_CTAS
+#define SENSEI_STENCIL_MIN_CTAS 2
+#endif
+
 namespace sensei {
 
 template <typename R>
@@ -278,7 +282,7 @@ __device__ __forceinline__ void to_recon(const double qd[NV], R gm1, int cons, b
 }
 
 template <typename R, int LIM, bool TWO_D>
-__global__ void __launch_bounds__(NTHREADS, 1) stencil_kernel(const StencilParams<R> p)
+__global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_kernel(const StencilParams<R> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SL = SmemLayout<R>;
@@ -321,9 +325,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) stencil_kernel(const StencilParam
     const bool update = p.out != nullptr;
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
 
-    double nsq[NV], nmax[NV], ncons[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) nsq[v] = nmax[v] = ncons[v] = 0.0;
+    // norm partials: reduced over each warp per plane, accumulated per warp
+    // in shared memory (keeps 15 FP64 accumulators out of the registers)
+    const int lane = t & 31, warp = t >> 5;
+    if (p.partials) {
+        for (int e = t; e < 3 * NV * (NTHREADS / 32); e += NTHREADS) sRed[e] = 0.0;
+    }
 
     // per-thread k-window of the own column: centre plane, the two above,
     // the plus-side k-state of the centre plane, the flux of its lower k-face
@@ -491,6 +498,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) stencil_kernel(const StencilParam
         __syncthreads();
 
         // ---- P3: residual, update, norms
+        double nsq[NV], nmax[NV], ncons[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) nsq[v] = nmax[v] = ncons[v] = 0.0;
         if (col_valid) {
             const long long cell = p.L.off + (long long)k * p.L.sk + (long long)cj * p.L.sj + ci;
             const long long mc = kpl + (long long)cj * p.ml.mpitch + ci;
@@ -515,9 +525,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) stencil_kernel(const StencilParam
                     p.Rout[v * nint + rc] = r;
                 }
                 if (p.partials) {
-                    nsq[v] += r * r;
-                    nmax[v] = fmax(nmax[v], fabs(r));
-                    ncons[v] += vol * uin;
+                    nsq[v] = r * r;
+                    nmax[v] = fabs(r);
+                    ncons[v] = vol * uin;
+                }
+            }
+        }
+        if (p.partials) {
+            // fixed-order warp tree, then the warp's own accumulator slot
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double a = nsq[v], b = nmax[v], c = ncons[v];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_down_sync(0xffffffffu, a, o);
+                    b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+                    c += __shfl_down_sync(0xffffffffu, c, o);
+                }
+                if (lane == 0) {
+                    sRed[(0 * NV + v) * (NTHREADS / 32) + warp] += a;
+                    sRed[(1 * NV + v) * (NTHREADS / 32) + warp] =
+                        fmax(sRed[(1 * NV + v) * (NTHREADS / 32) + warp], b);
+                    sRed[(2 * NV + v) * (NTHREADS / 32) + warp] += c;
                 }
             }
         }
@@ -535,24 +564,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) stencil_kernel(const StencilParam
         }
     }
 
-    // ---- FP64 norm partials of this CTA, fixed-order reduction
+    // ---- FP64 norm partials of this CTA: the warps' slots in a fixed order
     if (p.partials) {
-        const int lane = t & 31, warp = t >> 5;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            double a = nsq[v], b = nmax[v], c = ncons[v];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a += __shfl_down_sync(0xffffffffu, a, o);
-                b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
-                c += __shfl_down_sync(0xffffffffu, c, o);
-            }
-            if (lane == 0) {
-                sRed[(0 * NV + v) * (NTHREADS / 32) + warp] = a;
-                sRed[(1 * NV + v) * (NTHREADS / 32) + warp] = b;
-                sRed[(2 * NV + v) * (NTHREADS / 32) + warp] = c;
-            }
-        }
         __syncthreads();
         if (t < 3 * NV) {
             int kind = t / NV;
@@ -581,6 +594,10 @@ cudaError_t launch_stencil_t(const StencilParams<R> &p, int limiter, bool two_d,
     }
 #undef SENSEI_PICK
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // all of the unified L1/shared storage as shared memory, so that the
+    // register-limited number of CTAs per SM is not cut by the carveout
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     fn<<<grid, NTHREADS, smem, s>>>(p);
     return cudaGetLastError();
