@@ -65,17 +65,32 @@ def alg_flops_per_cell(limiter, two_d, alpha_nonzero, first_stage):
     return f
 
 
-def alg_bytes_per_cell(precision, alpha_nonzero, first_stage, two_d):
-    """Bytes the stencil kernel must move per interior cell and launch:
-    read U^(s-1) (40), write U^(s) (40), read U^n when blended (40), face
-    metrics (unit normal + area per face, 4 values x 3 faces) and 1/|Omega|
-    (8), and |Omega| (8) for the conservation sums on the first stage."""
+def alg_bytes_per_cell(form, stage, two_d, stages=3):
+    """Bytes the stencil kernel must move per interior cell in the launch of
+    RK stage `stage` (0-based) of an SSPRK3 step:
+      fp64 / fp32_flux: read U^(s-1) (40), write U^(s) (40), read U^n on the
+        stages that blend it (40), face metrics (unit normal + area of the
+        nd low faces: 32 B each in FP64, 16 B in FP32) and 1/|Omega| (8),
+        |Omega| (8) for the conservation sums on the first stage;
+      fp32_store: first stage reads U (40) and writes D, X (20 + 20); middle
+        stages read X (20), D (20), U^n (40) and write D, X (40); the last
+        reads X, D (40) and U^n (40) and writes U (40); FP32 face metrics and
+        1/|Omega| (4), |Omega| (8) on the first stage."""
     nd = 2 if two_d else 3
-    mbytes = 4 if precision == "fp32_flux" else 8
-    b = 40 + 40 + nd * 4 * mbytes + 8
-    if alpha_nonzero:
+    if form == "fp32_store":
+        b = nd * 16 + 4
+        if stage == 0:
+            b += 40 + 40 + 8
+        elif stage == stages - 1:
+            b += 40 + 40 + 40
+        else:
+            b += 40 + 40 + 40
+        return b
+    mbytes = 16 if form == "fp32_flux" else 32
+    b = 40 + 40 + nd * mbytes + 8
+    if stage > 0:
         b += 40
-    if first_stage:
+    else:
         b += 8
     return b
 
@@ -336,8 +351,7 @@ def main():
     alpha_frac = 2.0 / 3.0   # SSPRK3: stages 2 and 3 blend U^n
     flops = cells * (alg_flops_per_cell(w.limiter, two_d, False, True)
                      + alg_flops_per_cell(w.limiter, two_d, True, False) * 2) / 3.0
-    byts = cells * (alg_bytes_per_cell("fp64", False, True, two_d)
-                    + 2 * alg_bytes_per_cell("fp64", True, False, two_d)) / 3.0
+    byts = cells * sum(alg_bytes_per_cell("fp64", s_, two_d) for s_ in range(stages)) / stages
     peaks, peak_src = measured_peaks()
     sm_mhz = clk.get("sm_mhz") or 2070.0
     fp64_peak = fp64_peak_tflops(2070.0)
@@ -388,41 +402,42 @@ def main():
     line["e2e"] = {"value": units / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                    "d2h_bytes_per_step": state_bytes + 15 * 8}
 
-    # the mixed-precision form on the same workload: FP32 reconstruction and
-    # flux, FP64 state, update and norms; error vs the FP64 path (itself
-    # matched to the oracle) after the same steps from the same state
+    # the mixed-precision forms on the same workload: FP32 reconstruction and
+    # flux on the FP64 state (fp32_flux), and additionally FP32 stage storage
+    # with the FP64 accumulation U^{n+1} = U^n + D (fp32_store); error vs the
+    # FP64 path (itself matched to the oracle) after the same steps from the
+    # same state
     if not args.no_variants:
-        g32, U32 = gpu_setup(w, sensei.FP32_FLUX)
-        g64, U64 = gpu_setup(w, sensei.FP64)
-        for _ in range(args.warmup):
-            g32.rk_step(U32, rk, cfl=w.cfl)
-        ms32, prof32 = time_steps(g32, U32, args.steps, rk, w.cfl, profile=True)
         n_cmp = args.warmup + args.steps
+        g64, U64 = gpu_setup(w, sensei.FP64)
         for _ in range(n_cmp):
             g64.rk_step(U64, rk, cfl=w.cfl)
-        # repeat the mixed run from the start for an exact step count
-        g32b, U32b = gpu_setup(w, sensei.FP32_FLUX)
-        for _ in range(n_cmp):
-            g32b.rk_step(U32b, rk, cfl=w.cfl)
         torch.cuda.synchronize()
-        errs = []
-        for b in range(len(w.dims)):
-            a64 = g64.interior_view(U64[b], b)
-            a32 = g32b.interior_view(U32b[b], b)
-            errs.append((float(torch.linalg.vector_norm(a32[0] - a64[0])),
-                         float(torch.linalg.vector_norm(a64[0]))))
-        rho_l2 = math.sqrt(sum(e[0] ** 2 for e in errs)) / math.sqrt(sum(e[1] ** 2 for e in errs))
-        v32 = cells * stages * args.steps / (ms32 / 1e3)
-        st32 = prof32[0] / max(prof32[1], 1)
-        b32 = cells * (alg_bytes_per_cell("fp32_flux", False, True, two_d)
-                       + 2 * alg_bytes_per_cell("fp32_flux", True, False, two_d)) / 3.0
-        line["variants"] = {"fp32_flux": {
-            "value": v32, "unit": UNIT, "speedup_vs_fp64": v32 / value if world == 1 else None,
-            "rho_l2_rel_err_vs_fp64": rho_l2, "steps_compared": n_cmp,
-            "roofline": {"bound": "hbm", "achieved": b32 / (st32 / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
-                         "unit": "GB/s", "frac": b32 / (st32 / 1e3) / 1e9 / peaks["hbm_gbs"],
-                         "kernel_ms_per_launch": st32, "peak_source": peak_src}}}
-        del g32, U32, g64, U64, g32b, U32b
+        line["variants"] = {}
+        for vname, prec in (("fp32_flux", sensei.FP32_FLUX), ("fp32_store", sensei.FP32_STORE)):
+            gv, Uv = gpu_setup(w, prec)
+            for _ in range(args.warmup):
+                gv.rk_step(Uv, rk, cfl=w.cfl)
+            msv, profv = time_steps(gv, Uv, args.steps, rk, w.cfl, profile=True)
+            errs = []
+            for b in range(len(w.dims)):
+                a64 = g64.interior_view(U64[b], b)
+                av = gv.interior_view(Uv[b], b)
+                errs.append((float(torch.linalg.vector_norm(av[0] - a64[0])),
+                             float(torch.linalg.vector_norm(a64[0]))))
+            rho_l2 = math.sqrt(sum(e[0] ** 2 for e in errs)) / math.sqrt(sum(e[1] ** 2 for e in errs))
+            vv = cells * stages * args.steps / (msv / 1e3)
+            stv = profv[0] / max(profv[1], 1)
+            bv = cells * sum(alg_bytes_per_cell(vname, s_, two_d) for s_ in range(stages)) / stages
+            line["variants"][vname] = {
+                "value": vv, "unit": UNIT, "ms_per_step": msv / args.steps,
+                "speedup_vs_fp64": vv / value if world == 1 else None,
+                "rho_l2_rel_err_vs_fp64": rho_l2, "steps_compared": n_cmp,
+                "roofline": {"bound": "hbm", "achieved": bv / (stv / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                             "unit": "GB/s", "frac": bv / (stv / 1e3) / 1e9 / peaks["hbm_gbs"],
+                             "kernel_ms_per_launch": stv, "alg_bytes_per_launch": bv, "peak_source": peak_src}}
+            del gv, Uv
+        del g64, U64
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs, sample, _ = oracle_sample(args.workload, 3 if args.workload in ("c3", "c5") else 2, 0)

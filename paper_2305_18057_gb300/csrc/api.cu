@@ -43,8 +43,10 @@ struct Block {
     double *fn[3][4];
     float *fn32[3][4];
     double *vol, *ivol;
+    float *ivol32;
     double *sbar[3][4];
-    double *stage[2];
+    double *stage[2];       // FP64 stage states (FP64, FP32-flux)
+    float *xs[2], *ds[2];   // FP32 stage states and increments (FP32 storage)
     int tiles_i, tiles_j, kchunk, nchunks;
     long long part_off;   // first partial slot (CTA index) of this block
     int nparts;
@@ -63,7 +65,7 @@ struct Plan {
     long long nparts = 0;
     long long ncells = 0;
     // per-block offsets (same order as the Block fields)
-    std::vector<size_t> off_fn, off_fn32, off_vol, off_ivol, off_sbar, off_stage;
+    std::vector<size_t> off_fn, off_fn32, off_vol, off_ivol, off_ivol32, off_sbar, off_stage;
 };
 
 size_t take(size_t &cursor, size_t bytes)
@@ -81,8 +83,6 @@ sensei_status check_scheme(const sensei_scheme *s)
         return fail(SENSEI_ERR_INVALID_ARG, "unknown limiter %d", s->limiter);
     if (s->precision < SENSEI_FP64 || s->precision > SENSEI_FP32_STORE)
         return fail(SENSEI_ERR_INVALID_ARG, "unknown precision %d", s->precision);
-    if (s->precision == SENSEI_FP32_STORE)
-        return fail(SENSEI_ERR_UNSUPPORTED, "SENSEI_FP32_STORE is not implemented by this build");
     if (!(s->entropy_fix >= 0.0)) return fail(SENSEI_ERR_INVALID_ARG, "entropy_fix must be >= 0");
     if (!(s->eps >= 0.0 && s->eps <= 1.0)) return fail(SENSEI_ERR_INVALID_ARG, "eps must lie in [0, 1]");
     if (!(s->kappa >= -1.0 && s->kappa <= 1.0)) return fail(SENSEI_ERR_INVALID_ARG, "kappa must lie in [-1, 1]");
@@ -100,6 +100,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     P.off_fn32.resize(nblocks);
     P.off_vol.resize(nblocks);
     P.off_ivol.resize(nblocks);
+    P.off_ivol32.resize(nblocks);
     P.off_sbar.resize(nblocks);
     P.off_stage.resize(nblocks);
     const bool f32 = scheme->precision != SENSEI_FP64;
@@ -150,7 +151,9 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         P.off_fn32[b] = f32 ? take(cur, 12 * mv * sizeof(float)) : 0;
         P.off_vol[b] = take(cur, mv * sizeof(double));
         P.off_ivol[b] = take(cur, mv * sizeof(double));
+        P.off_ivol32[b] = f32 ? take(cur, mv * sizeof(float)) : 0;
         P.off_sbar[b] = take(cur, 12 * mv * sizeof(double));
+        // two FP64 stage states, or two FP32 stage states + two FP32 increments
         P.off_stage[b] = take(cur, 2 * (size_t)B.L.elems * sizeof(double));
     }
     if (P.nparts > (1LL << 30)) return fail(SENSEI_ERR_INVALID_ARG, "grid too large");
@@ -242,17 +245,19 @@ CellMetrics cell_metrics(const Block &B)
     CellMetrics cm;
     cm.vol = B.vol;
     cm.ivol = B.ivol;
+    cm.ivol32 = B.ivol32;
     for (int d = 0; d < 3; ++d)
         for (int q = 0; q < 4; ++q) cm.sbar[d][q] = B.sbar[d][q];
     return cm;
 }
 
-sensei_status fill_ghosts_impl(sensei_grid *g, double *const *U, cudaStream_t s)
+template <typename T>
+sensei_status fill_ghosts_impl(sensei_grid *g, T *const *U, cudaStream_t s)
 {
     const auto &blocks = g->plan.blocks;
     for (size_t b = 0; b < blocks.size(); ++b) {
         const Block &B = blocks[b];
-        BCParams p;
+        BCParamsT<T> p;
         memset(&p, 0, sizeof p);
         p.ni = B.ni;
         p.nj = B.nj;
@@ -265,7 +270,7 @@ sensei_status fill_ghosts_impl(sensei_grid *g, double *const *U, cudaStream_t s)
         for (int fam = 0; fam < 3; ++fam)
             for (int q = 0; q < 4; ++q) p.fm.n[fam][q] = B.fn[fam][q];
         for (int f = 0; f < p.nfaces; ++f) {
-            FaceBC &fb = p.f[f];
+            FaceBC<T> &fb = p.f[f];
             fb.type = B.bc_type[f];
             memcpy(fb.prim, B.bc_prim[f], sizeof fb.prim);
             long long n1 = f < 2 ? B.nj : B.ni;
@@ -317,9 +322,13 @@ void fill_common(StencilParams<R> &p, const sensei_grid *g, const Block &B)
 }
 
 struct StencilCall {
-    const double *in;
+    int mode;
+    const void *in;
+    bool in_f32;            // the stage input is an FP32 stage state
     const double *un;
     double *out;
+    const float *dprev;
+    float *dout, *xout;
     double *Rout;
     const double *src;
     double alpha, beta, gdt;
@@ -362,6 +371,7 @@ sensei_status stencil_launch(sensei_grid *g, const Block &B, const StencilCall &
         fill_common(p, g, B);
         for (int fam = 0; fam < 3; ++fam)
             for (int q = 0; q < 4; ++q) p.fm.n[fam][q] = B.fn[fam][q];
+        p.mode = c.mode;
         p.in = c.in;
         p.un = c.un;
         p.out = c.out;
@@ -380,9 +390,13 @@ sensei_status stencil_launch(sensei_grid *g, const Block &B, const StencilCall &
         fill_common(p, g, B);
         for (int fam = 0; fam < 3; ++fam)
             for (int q = 0; q < 4; ++q) p.fm.n[fam][q] = B.fn32[fam][q];
+        p.mode = c.mode;
         p.in = c.in;
         p.un = c.un;
         p.out = c.out;
+        p.dprev = c.dprev;
+        p.dout = c.dout;
+        p.xout = c.xout;
         p.Rout = c.Rout;
         p.src = c.src;
         p.alpha = c.alpha;
@@ -391,7 +405,10 @@ sensei_status stencil_launch(sensei_grid *g, const Block &B, const StencilCall &
         p.dt_slot = c.dt_slot;
         p.dt_scale = c.dt_scale;
         p.partials = c.partials ? g->partials + B.part_off * 3 * NV : nullptr;
-        CUDA_TRY(launch_stencil_f32(p, g->scheme.limiter, B.two_d, s));
+        if (c.in_f32)
+            CUDA_TRY(launch_stencil_f32s(p, g->scheme.limiter, B.two_d, s));
+        else
+            CUDA_TRY(launch_stencil_f32(p, g->scheme.limiter, B.two_d, s));
     }
     return SENSEI_OK;
 }
@@ -492,8 +509,14 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
             }
         B.vol = (double *)(g->ws + P.off_vol[b]);
         B.ivol = (double *)(g->ws + P.off_ivol[b]);
+        B.ivol32 = P.off_ivol32[b] ? (float *)(g->ws + P.off_ivol32[b]) : nullptr;
         B.stage[0] = (double *)(g->ws + P.off_stage[b]);
         B.stage[1] = B.stage[0] + B.L.elems;
+        // FP32 storage reuses the same bytes: X0, X1, D0, D1
+        B.xs[0] = (float *)B.stage[0];
+        B.xs[1] = B.xs[0] + B.L.elems;
+        B.ds[0] = B.xs[1] + B.L.elems;
+        B.ds[1] = B.ds[0] + B.L.elems;
         for (int f = 0; f < 6; ++f) {
             B.bc_set[f] = false;
             B.nbr[f] = -1;
@@ -509,6 +532,7 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
             }
         mo.vol = B.vol;
         mo.ivol = B.ivol;
+        mo.ivol32 = B.ivol32;
         cudaError_t e = launch_metrics(B.ni, B.nj, B.nk, nodes[b], mo, B.ml, s);
         if (e != cudaSuccess) {
             delete g;
@@ -628,6 +652,7 @@ sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const
     for (size_t b = 0; b < blocks.size(); ++b) {
         StencilCall c;
         memset(&c, 0, sizeof c);
+        c.mode = MODE_RESIDUAL;
         c.in = U[b];
         c.Rout = R[b];
         c.src = src ? src[b] : nullptr;
@@ -683,31 +708,69 @@ sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double
     }
 
     const int S = RK_STAGES[rk];
+    const bool incr = grid->scheme.precision == SENSEI_FP32_STORE;
     std::vector<double *> in(nb), outp(nb);
+    std::vector<float *> xin(nb);
     for (int stage = 0; stage < S; ++stage) {
-        for (int b = 0; b < nb; ++b) {
-            in[b] = stage == 0 ? U[b] : blocks[b].stage[(stage - 1) % 2];
-            outp[b] = stage == S - 1 ? U[b] : blocks[b].stage[stage % 2];
-        }
-        if (stage > 0) {
-            st = fill_ghosts_impl(grid, in.data(), s);
-            if (st != SENSEI_OK) return st;
-        }
         const double *co = RK_COEF[rk][stage];
-        for (int b = 0; b < nb; ++b) {
-            StencilCall c;
-            memset(&c, 0, sizeof c);
-            c.in = in[b];
-            c.un = co[0] != 0.0 ? U[b] : nullptr;
-            c.out = outp[b];
-            c.alpha = co[0];
-            c.beta = co[1];
-            c.gdt = co[2];
-            c.dt_slot = dt_src;
-            c.dt_scale = dt_scale;
-            c.partials = stage == 0;
-            st = stencil(grid, blocks[b], c, s);
-            if (st != SENSEI_OK) return st;
+        const bool last = stage == S - 1;
+        if (!incr) {
+            // FP64 stage states: U -> st0 -> st1 -> ... -> U
+            for (int b = 0; b < nb; ++b) {
+                in[b] = stage == 0 ? U[b] : blocks[b].stage[(stage - 1) % 2];
+                outp[b] = last ? U[b] : blocks[b].stage[stage % 2];
+            }
+            if (stage > 0) {
+                st = fill_ghosts_impl(grid, in.data(), s);
+                if (st != SENSEI_OK) return st;
+            }
+            for (int b = 0; b < nb; ++b) {
+                StencilCall c;
+                memset(&c, 0, sizeof c);
+                c.mode = MODE_ACCUM;
+                c.in = in[b];
+                c.un = co[0] != 0.0 ? U[b] : nullptr;
+                c.out = outp[b];
+                c.alpha = co[0];
+                c.beta = co[1];
+                c.gdt = co[2];
+                c.dt_slot = dt_src;
+                c.dt_scale = dt_scale;
+                c.partials = stage == 0;
+                st = stencil(grid, blocks[b], c, s);
+                if (st != SENSEI_OK) return st;
+            }
+        } else {
+            // FP32 storage: the first stage reads the FP64 master U, later
+            // stages the FP32 stage state X^(s-1); every stage but the last
+            // writes the FP32 increment D^(s) and X^(s); the last adds its
+            // increment to U in FP64.
+            if (stage > 0) {
+                for (int b = 0; b < nb; ++b) xin[b] = blocks[b].xs[(stage - 1) % 2];
+                st = fill_ghosts_impl(grid, xin.data(), s);
+                if (st != SENSEI_OK) return st;
+            }
+            for (int b = 0; b < nb; ++b) {
+                const Block &B = blocks[b];
+                StencilCall c;
+                memset(&c, 0, sizeof c);
+                c.mode = MODE_INCR;
+                c.in = stage == 0 ? (const void *)U[b] : (const void *)B.xs[(stage - 1) % 2];
+                c.in_f32 = stage > 0;
+                c.un = U[b];
+                c.dprev = stage == 0 ? nullptr : B.ds[(stage - 1) % 2];
+                c.out = last ? U[b] : nullptr;
+                c.dout = last ? nullptr : B.ds[stage % 2];
+                c.xout = last ? nullptr : B.xs[stage % 2];
+                c.alpha = co[0];
+                c.beta = co[1];
+                c.gdt = co[2];
+                c.dt_slot = dt_src;
+                c.dt_scale = dt_scale;
+                c.partials = stage == 0;
+                st = stencil(grid, B, c, s);
+                if (st != SENSEI_OK) return st;
+            }
         }
     }
     CUDA_TRY(launch_norms_finalize(grid->partials, (int)grid->plan.nparts, grid->plan.ncells, grid->norms, s));

@@ -110,6 +110,7 @@ __global__ void metrics_kernel(int ni, int nj, int nk, const double *__restrict_
             vol = vol / 3.0;
             mo.vol[m] = vol;
             mo.ivol[m] = 1.0 / vol;
+            if (mo.ivol32) mo.ivol32[m] = (float)(1.0 / vol);
         }
     }
 }
@@ -138,7 +139,8 @@ __device__ __forceinline__ void face_cells(int f, int ni, int nj, int nk, int t1
     }
 }
 
-__global__ void bc_kernel(BCParams p)
+template <typename T>
+__global__ void bc_kernel(BCParamsT<T> p)
 {
     long long total = 0;
     for (int f = 0; f < p.nfaces; ++f) total += p.count[f];
@@ -155,9 +157,9 @@ __global__ void bc_kernel(BCParams p)
         long long pos = r / 2;
         int t1 = (int)(pos % n1);
         int t2 = (int)(pos / n1);
-        const FaceBC &bc = p.f[f];
+        const FaceBC<T> &bc = p.f[f];
         int gi, gj, gk, mi, mj, mk;
-        double q[NV];
+        T q[NV];
         if (bc.type == SENSEI_BC_PERIODIC || bc.type == SENSEI_BC_SLIP_WALL) {
             // periodic: the opposite face's layer-1 cell inside; wall: mirror
             int src_face = bc.type == SENSEI_BC_PERIODIC ? (f ^ 1) : f;
@@ -176,11 +178,11 @@ __global__ void bc_kernel(BCParams p)
                 if (f == 2) bj = 0;
                 if (f == 4) bk = 0;
                 long long fm = bk * p.ml.mplane + bj * p.ml.mpitch + bi;
-                double nx = p.fm.n[fam][0][fm], ny = p.fm.n[fam][1][fm], nz = p.fm.n[fam][2][fm];
-                double mn = q[1] * nx + q[2] * ny + q[3] * nz;
-                q[1] -= 2.0 * mn * nx;
-                q[2] -= 2.0 * mn * ny;
-                q[3] -= 2.0 * mn * nz;
+                const T nx = (T)p.fm.n[fam][0][fm], ny = (T)p.fm.n[fam][1][fm], nz = (T)p.fm.n[fam][2][fm];
+                const T mn = q[1] * nx + q[2] * ny + q[3] * nz;
+                q[1] -= T(2) * mn * nx;
+                q[2] -= T(2) * mn * ny;
+                q[3] -= T(2) * mn * nz;
             }
         } else if (bc.type == SENSEI_BC_EXTRAPOLATE) {
             face_cells(f, p.ni, p.nj, p.nk, t1, t2, layer, 0, gi, gj, gk, mi, mj, mk);
@@ -189,11 +191,11 @@ __global__ void bc_kernel(BCParams p)
         } else if (bc.type == SENSEI_BC_INFLOW) {
             face_cells(f, p.ni, p.nj, p.nk, t1, t2, layer, 0, gi, gj, gk, mi, mj, mk);
             double rho = bc.prim[0], u = bc.prim[1], v = bc.prim[2], w = bc.prim[3], pr = bc.prim[4];
-            q[0] = rho;
-            q[1] = rho * u;
-            q[2] = rho * v;
-            q[3] = rho * w;
-            q[4] = pr / (p.gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w);
+            q[0] = (T)rho;
+            q[1] = (T)(rho * u);
+            q[2] = (T)(rho * v);
+            q[3] = (T)(rho * w);
+            q[4] = (T)(pr / (p.gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w));
         } else {   // SENSEI_BC_INTERFACE: neighbour's layer-1 cell inside its face
             int a, b, c;
             face_cells(f, p.ni, p.nj, p.nk, t1, t2, layer, 0, gi, gj, gk, a, b, c);
@@ -218,15 +220,19 @@ cudaError_t launch_metrics(int ni, int nj, int nk, const double *X, const Metric
     return cudaGetLastError();
 }
 
-cudaError_t launch_bc(const BCParams &p, cudaStream_t s)
+template <typename T>
+static cudaError_t launch_bc_t(const BCParamsT<T> &p, cudaStream_t s)
 {
     long long total = 0;
     for (int f = 0; f < p.nfaces; ++f) total += p.count[f];
     if (total == 0) return cudaSuccess;
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    bc_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+    bc_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
+
+cudaError_t launch_bc(const BCParamsT<double> &p, cudaStream_t s) { return launch_bc_t(p, s); }
+cudaError_t launch_bc(const BCParamsT<float> &p, cudaStream_t s) { return launch_bc_t(p, s); }
 
 }  // namespace sensei

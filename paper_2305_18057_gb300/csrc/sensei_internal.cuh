@@ -45,6 +45,7 @@ struct FaceMetrics {
 struct CellMetrics {
     const double *vol;      // |Omega|
     const double *ivol;     // 1 / |Omega|
+    const float *ivol32;    // 1 / |Omega| rounded to FP32 (FP32-storage stages)
     const double *sbar[3][4];   // per direction d: mean area vector of the two d-faces (3), its length
 };
 
@@ -57,21 +58,37 @@ struct MetricsOut {
     double *n[3][4];
     float *n32[3][4];       // FP32 copies for the FP32-flux stencil (may be null)
     double *vol, *ivol;
+    float *ivol32;          // may be null
     double *sbar[3][4];
 };
 
 // ------------------------------------------------------------------------
-// Stencil launch: residual mode (write R) or Runge-Kutta stage mode
-//   out = alpha * Un + beta * in - gdt * dt * ivol * R
+// Stencil launch modes:
+//   MODE_RESIDUAL  write R
+//   MODE_ACCUM     Runge-Kutta stage with an FP64 stage state:
+//                    out = alpha * Un + beta * in - gdt * dt * ivol * R
+//   MODE_INCR      Runge-Kutta stage with FP32 stage storage: the FP32
+//                  increment D = U^(s) - U^n,
+//                    D = beta * Dprev - gdt * dt * ivol * R,
+//                  stored with the FP32 stage state X = float(U^n) + D
+//                  (dout, xout), or on the last stage accumulated in FP64,
+//                    out = Un + D.
+// The stage input `in` is FP64 (TS = double) or FP32 (TS = float) with the
+// element strides of StateLayout.
 // ------------------------------------------------------------------------
+enum { MODE_RESIDUAL = 0, MODE_ACCUM = 1, MODE_INCR = 2 };
+
 template <typename R>
 struct StencilParams {
     int ni, nj, nk;
     int tiles_i, tiles_j, kchunk, nchunks;
     StateLayout L;
-    const double *in;       // stage input (ghosts filled)
-    const double *un;       // U^n (null when alpha == 0)
-    double *out;            // stage output (null in residual mode)
+    int mode;
+    const void *in;         // stage input (ghosts filled), double or float
+    const double *un;       // U^n (null when not needed)
+    double *out;            // FP64 stage output
+    const float *dprev;     // MODE_INCR: previous increment (null on the first stage)
+    float *dout, *xout;     // MODE_INCR: increment and FP32 stage state (null on the last stage)
     double *Rout;           // residual R[5][nk][nj][ni] (residual mode)
     const double *src;      // |Omega| S_h, same layout as Rout (may be null)
     FaceMetrics<R> fm;
@@ -86,36 +103,45 @@ struct StencilParams {
     unsigned *err;
 };
 
-// Boundary fill of one block: 6 faces.
+// Boundary fill of one block: 6 faces; T = double (state) or float (FP32
+// stage state).
+template <typename T>
 struct FaceBC {
     int type;
     double prim[NV];
-    const double *nbr;      // neighbour block state (INTERFACE)
+    const T *nbr;           // neighbour block state (INTERFACE)
     StateLayout nL;
     int nni, nnj, nnk;      // neighbour dims
     int nbr_face;
 };
 
-struct BCParams {
+template <typename T>
+struct BCParamsT {
     int ni, nj, nk;
     StateLayout L;
-    double *U;
-    FaceBC f[6];
+    T *U;
+    FaceBC<T> f[6];
     int nfaces;             // 4 in 2D, 6 in 3D
     long long count[6];     // work items per face (positions x layers)
     double gamma;
     FaceMetrics<double> fm;
     MetricLayout ml;
 };
+using BCParams = BCParamsT<double>;
 
 // ------------------------------------------------------------------------
 // host-side launchers (defined in the .cu files)
 // ------------------------------------------------------------------------
 cudaError_t launch_metrics(int ni, int nj, int nk, const double *X, const MetricsOut &mo,
                            const MetricLayout &ml, cudaStream_t s);
-cudaError_t launch_bc(const BCParams &p, cudaStream_t s);
+cudaError_t launch_bc(const BCParamsT<double> &p, cudaStream_t s);
+cudaError_t launch_bc(const BCParamsT<float> &p, cudaStream_t s);
+// FP64 arithmetic on an FP64 state
 cudaError_t launch_stencil_f64(const StencilParams<double> &p, int limiter, bool two_d, cudaStream_t s);
+// FP32 arithmetic on an FP64 state (FP32 flux; first FP32-storage stage; residuals)
 cudaError_t launch_stencil_f32(const StencilParams<float> &p, int limiter, bool two_d, cudaStream_t s);
+// FP32 arithmetic on an FP32 stage state
+cudaError_t launch_stencil_f32s(const StencilParams<float> &p, int limiter, bool two_d, cudaStream_t s);
 cudaError_t launch_dt(int ni, int nj, int nk, const StateLayout &L, const double *U, const CellMetrics &cm,
                       const MetricLayout &ml, double gamma, unsigned long long *dt_bits, unsigned *err,
                       cudaStream_t s);

@@ -243,25 +243,26 @@ __device__ __forceinline__ void face_flux(R L[NV], R Rt[NV], R nx, R ny, R nz, R
     }
 }
 
-template <typename R>
+// Loads a cell of the stage input (storage type TS) as the arithmetic type R.
+template <typename R, typename TS>
 struct CellLoader {
-    const double *in;
+    const TS *in;
     StateLayout L;
     int ni, nj, nk;
     __device__ __forceinline__ bool inside(int i, int j, int k) const
     {
         return i >= -NG && i < ni + NG && j >= -NG && j < nj + NG && k >= -L.gk && k < nk + L.gk;
     }
-    __device__ __forceinline__ void raw(int i, int j, int k, double q[NV]) const
+    __device__ __forceinline__ void raw(int i, int j, int k, R q[NV]) const
     {
         if (inside(i, j, k)) {
-            const double *c = in + L.off + (long long)k * L.sk + (long long)j * L.sj + i;
+            const TS *c = in + L.off + (long long)k * L.sk + (long long)j * L.sj + i;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) q[v] = __ldg(c + v * L.sv);
+            for (int v = 0; v < NV; ++v) q[v] = (R)__ldg(c + v * L.sv);
         } else {   // outside the ghosted box: a harmless state, never used by a valid face
-            q[0] = 1.0;
-            q[1] = q[2] = q[3] = 0.0;
-            q[4] = 2.5;
+            q[0] = R(1);
+            q[1] = q[2] = q[3] = R(0);
+            q[4] = R(2.5);
         }
     }
 };
@@ -269,11 +270,8 @@ struct CellLoader {
 // Convert a loaded cell to the reconstructed variables; flag non-physical
 // interior cells.
 template <typename R>
-__device__ __forceinline__ void to_recon(const double qd[NV], R gm1, int cons, bool interior, unsigned *err, R out[NV])
+__device__ __forceinline__ void to_recon(const R q[NV], R gm1, int cons, bool interior, unsigned *err, R out[NV])
 {
-    R q[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) q[v] = (R)qd[v];
     R w[NV];
     bool ok = to_prim(q, gm1, w);
     if (interior && !ok) atomicOr(err, ERR_NONPHYSICAL);
@@ -281,7 +279,7 @@ __device__ __forceinline__ void to_recon(const double qd[NV], R gm1, int cons, b
     for (int v = 0; v < NV; ++v) out[v] = cons ? q[v] : w[v];
 }
 
-template <typename R, int LIM, bool TWO_D>
+template <typename R, typename TS, int LIM, bool TWO_D>
 __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_kernel(const StencilParams<R> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -321,22 +319,24 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
     const R half_eps = p.eps / R(2);
     const int cons = p.cons;
 
-    CellLoader<R> ld{p.in, p.L, p.ni, p.nj, p.nk};
-    const bool update = p.out != nullptr;
+    const TS *in = static_cast<const TS *>(p.in);
+    CellLoader<R, TS> ld{in, p.L, p.ni, p.nj, p.nk};
+    const bool update = p.mode != MODE_RESIDUAL;
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
+    const float gdt_dt32 = (float)(p.gdt * dt);   // MODE_INCR
+    const float beta32 = (float)p.beta;
 
-    // norm partials: reduced over each warp per plane, accumulated per warp
-    // in shared memory (keeps 15 FP64 accumulators out of the registers)
-    const int lane = t & 31, warp = t >> 5;
-    if (p.partials) {
-        for (int e = t; e < 3 * NV * (NTHREADS / 32); e += NTHREADS) sRed[e] = 0.0;
-    }
+    // per-thread FP64 norm accumulators (touched once per plane; under the
+    // 2-CTA register budget the compiler may keep them in local memory)
+    double nsq[NV], nmax[NV], ncons[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) nsq[v] = nmax[v] = ncons[v] = 0.0;
 
     // per-thread k-window of the own column: centre plane, the two above,
     // the plus-side k-state of the centre plane, the flux of its lower k-face
     R Wc[NV], W1[NV], W2[NV], Pp[NV], Fkm[NV];
     if (!TWO_D) {
-        double q[NV];
+        R q[NV];
         R Wm2[NV], Wm1[NV];
         ld.raw(ci, cj, k0 - 2, q);
         to_recon(q, gm1, cons, false, p.err, Wm2);
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
 
     for (int k = k0; k < k1; ++k) {
         // ---- P0: the centre plane with its halo into shared memory
-        double pre[NV];
+        R pre[NV];
         if (!TWO_D) {
             ld.raw(ci, cj, k + 3, pre);   // prefetch the plane entering the window
 #pragma unroll
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
                     c = e2 % TI;
                     r = s < 2 ? s - 2 : TJ + s - 2;
                 }
-                double q[NV];
+                R q[NV];
                 R w[NV];
                 ld.raw(i0 + c, j0 + r, k, q);
                 to_recon(q, gm1, cons, false, p.err, w);
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
                 int r = e / (TI + 4) - 2, c = e % (TI + 4) - 2;
                 bool corner = (r < 0 || r >= TJ) && (c < 0 || c >= TI);
                 if (corner) continue;
-                double q[NV];
+                R q[NV];
                 R w[NV];
                 int gi = i0 + c, gj = j0 + r;
                 ld.raw(gi, gj, 0, q);
@@ -498,9 +498,6 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
         __syncthreads();
 
         // ---- P3: residual, update, norms
-        double nsq[NV], nmax[NV], ncons[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) nsq[v] = nmax[v] = ncons[v] = 0.0;
         if (col_valid) {
             const long long cell = p.L.off + (long long)k * p.L.sk + (long long)cj * p.L.sj + ci;
             const long long mc = kpl + (long long)cj * p.ml.mpitch + ci;
@@ -516,42 +513,36 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
                 if (!TWO_D) rr += Fkp[v] - Fkm[v];
                 double r = (double)rr;
                 if (p.src) r -= p.src[v * nint + rc];
-                const double uin = p.in[cell + v * p.L.sv];
-                if (update) {
+                const double uin = (double)in[cell + v * p.L.sv];
+                if (p.mode == MODE_ACCUM) {
                     double val = p.beta * uin + coef * r;
                     if (p.un) val += p.alpha * p.un[cell + v * p.L.sv];
                     p.out[cell + v * p.L.sv] = val;
+                } else if (p.mode == MODE_INCR) {
+                    // FP32 increment; FP64 accumulation on the last stage
+                    float delta = -(gdt_dt32 * p.cm.ivol32[mc]) * (float)rr;
+                    if (p.dprev) delta = fmaf(beta32, p.dprev[cell + v * p.L.sv], delta);
+                    if (p.out) {
+                        p.out[cell + v * p.L.sv] = p.un[cell + v * p.L.sv] + (double)delta;
+                    } else {
+                        // the FP32 image of U^n: the loaded input on the
+                        // first stage, else rounded from the FP64 master
+                        float xc = sizeof(TS) == 8 ? (float)in[cell + v * p.L.sv] : (float)p.un[cell + v * p.L.sv];
+                        p.dout[cell + v * p.L.sv] = delta;
+                        p.xout[cell + v * p.L.sv] = xc + delta;
+                    }
                 } else {
                     p.Rout[v * nint + rc] = r;
                 }
                 if (p.partials) {
-                    nsq[v] = r * r;
-                    nmax[v] = fabs(r);
-                    ncons[v] = vol * uin;
-                }
-            }
-        }
-        if (p.partials) {
-            // fixed-order warp tree, then the warp's own accumulator slot
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                double a = nsq[v], b = nmax[v], c = ncons[v];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    a += __shfl_down_sync(0xffffffffu, a, o);
-                    b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
-                    c += __shfl_down_sync(0xffffffffu, c, o);
-                }
-                if (lane == 0) {
-                    sRed[(0 * NV + v) * (NTHREADS / 32) + warp] += a;
-                    sRed[(1 * NV + v) * (NTHREADS / 32) + warp] =
-                        fmax(sRed[(1 * NV + v) * (NTHREADS / 32) + warp], b);
-                    sRed[(2 * NV + v) * (NTHREADS / 32) + warp] += c;
+                    nsq[v] = fma(r, r, nsq[v]);
+                    nmax[v] = fmax(nmax[v], fabs(r));
+                    ncons[v] = fma(vol, uin, ncons[v]);
                 }
             }
         }
         if (!TWO_D) {
-            double q[NV];
+            R q[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 Fkm[v] = Fkp[v];
@@ -564,8 +555,24 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
         }
     }
 
-    // ---- FP64 norm partials of this CTA: the warps' slots in a fixed order
+    // ---- FP64 norm partials of this CTA, fixed-order reduction
     if (p.partials) {
+        const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double a = nsq[v], b = nmax[v], c = ncons[v];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_down_sync(0xffffffffu, a, o);
+                b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+                c += __shfl_down_sync(0xffffffffu, c, o);
+            }
+            if (lane == 0) {
+                sRed[(0 * NV + v) * (NTHREADS / 32) + warp] = a;
+                sRed[(1 * NV + v) * (NTHREADS / 32) + warp] = b;
+                sRed[(2 * NV + v) * (NTHREADS / 32) + warp] = c;
+            }
+        }
         __syncthreads();
         if (t < 3 * NV) {
             int kind = t / NV;
@@ -579,14 +586,14 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
     }
 }
 
-template <typename R>
+template <typename R, typename TS>
 cudaError_t launch_stencil_t(const StencilParams<R> &p, int limiter, bool two_d, cudaStream_t s)
 {
     const size_t smem = SmemLayout<R>::bytes;
     const unsigned grid = (unsigned)((long long)p.tiles_i * p.tiles_j * (two_d ? 1 : p.nchunks));
     void (*fn)(const StencilParams<R>) = nullptr;
 #define SENSEI_PICK(L)                                                                                  \
-    fn = two_d ? stencil_kernel<R, L, true> : stencil_kernel<R, L, false>;
+    fn = two_d ? stencil_kernel<R, TS, L, true> : stencil_kernel<R, TS, L, false>;
     switch (limiter) {
     case SENSEI_LIM_NONE: SENSEI_PICK(SENSEI_LIM_NONE); break;
     case SENSEI_LIM_MINMOD: SENSEI_PICK(SENSEI_LIM_MINMOD); break;

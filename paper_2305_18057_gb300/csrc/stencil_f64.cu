@@ -4,6 +4,6 @@
 namespace sensei {
 cudaError_t launch_stencil_f64(const StencilParams<double> &p, int limiter, bool two_d, cudaStream_t s)
 {
-    return launch_stencil_t<double>(p, limiter, two_d, s);
+    return launch_stencil_t<double, double>(p, limiter, two_d, s);
 }
 }  // namespace sensei

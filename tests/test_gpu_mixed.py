@@ -1,7 +1,9 @@
-"""Mixed precision (FP32 reconstruction and flux, FP64 state, update and
-norms) against the FP64 oracle: no closed form fixes this error, so it is
-measured and bounded.  Target: density L2 error <= 1e-5 relative to the
-oracle after many steps; each residual within FP32 rounding of the flux."""
+"""Mixed precision against the FP64 oracle: FP32 reconstruction and flux on
+an FP64 state (FP32_FLUX), and additionally FP32 stage storage with the FP64
+accumulation U^{n+1} = U^n + D (FP32_STORE).  No closed form fixes this
+error, so it is measured and bounded.  Target: density L2 error <= 1e-5
+relative to the oracle after many steps; each residual within FP32
+rounding of the flux; conservation sums still FP64-exact."""
 import numpy as np
 import pytest
 
@@ -34,22 +36,25 @@ def test_fp32_flux_residual_close_to_oracle(case):
         assert per_var_rel(Rs[b].cpu().numpy(), Ro[b]) < 2e-4, (case, b)
 
 
-@pytest.mark.parametrize("case,steps", [("periodic3d", 100), ("ramp2d", 100), ("advection2d", 100)])
-def test_fp32_flux_state_error_within_target(case, steps):
+@pytest.mark.parametrize("precision", ["fp32_flux", "fp32_store"])
+@pytest.mark.parametrize("case,steps", [("periodic3d", 100), ("ramp2d", 100), ("advection2d", 100),
+                                        ("lattice", 60)])
+def test_mixed_state_error_within_target(case, steps, precision):
     w = {"periodic3d": lambda: wl.periodic_3d(n=24, nj=16, nk=12, seed=8),
          "ramp2d": lambda: wl.ramp_2d(ni=70, nj=33, ratio=1.03, perturb=0.05),
-         "advection2d": lambda: wl.advection_2d(n=48)}[case]()
+         "advection2d": lambda: wl.advection_2d(n=48),
+         "lattice": lambda: wl.lattice_3d(sizes=(6, 9, 13), nblk=(2, 2, 2), seed=4, perturb=0.05)}[case]()
     og = oracle_grid(w)
     Uo = oracle_states(og, w)
-    g = gpu_grid(w, precision=sensei.FP32_FLUX)
+    g = gpu_grid(w, precision={"fp32_flux": sensei.FP32_FLUX, "fp32_store": sensei.FP32_STORE}[precision])
     Us = gpu_states(g, w)
     dt_used = torch.zeros(1, dtype=torch.float64, device=Us[0].device)
     for _ in range(steps):
         g.rk_step(Us, sensei.RK3_SSP, cfl=0.5, dt_used=dt_used)
         og.rk_step(Uo, 1, dt=dt_used.item())
     torch.cuda.synchronize()
-    got = g.download(Us[0], 0)
-    want = og.interior(Uo[0], 0)
+    got = np.concatenate([g.download(Us[b], b).reshape(5, -1) for b in range(len(w.dims))], axis=1)
+    want = np.concatenate([og.interior(Uo[b], b).reshape(5, -1) for b in range(len(w.dims))], axis=1)
     err_rho = _l2_rel(got[0], want[0])
     assert err_rho <= 1e-5, err_rho
     # momentum and energy: same order
@@ -57,16 +62,20 @@ def test_fp32_flux_state_error_within_target(case, steps):
         assert _l2_rel(got[q], want[q]) <= 1e-4, q
 
 
-def test_fp32_flux_conserves_mass_to_round_off():
+@pytest.mark.parametrize("precision", ["fp32_flux", "fp32_store"])
+def test_mixed_conserves_mass_to_round_off(precision):
     w = wl.periodic_3d(n=24, nj=16, nk=12, seed=8)
-    g = gpu_grid(w, precision=sensei.FP32_FLUX)
+    g = gpu_grid(w, precision={"fp32_flux": sensei.FP32_FLUX, "fp32_store": sensei.FP32_STORE}[precision])
     Us = gpu_states(g, w)
     g.rk_step(Us, sensei.RK3_SSP, cfl=0.5)
     st, _, _, cons0 = g.norms()
     for _ in range(50):
         g.rk_step(Us, sensei.RK3_SSP, cfl=0.5)
     st, _, _, cons1 = g.norms()
-    # each FP32 face flux enters its two cells with opposite signs, so the
-    # FP64 sums of |Omega| U telescope exactly up to FP64 round-off
-    assert abs(cons1[0] - cons0[0]) <= 1e-12 * abs(cons0[0])
-    assert abs(cons1[4] - cons0[4]) <= 1e-12 * abs(cons0[4])
+    # each FP32 face flux enters its two cells with opposite signs; the
+    # per-cell FP32 sums and (FP32_STORE) the FP32 increments round, so the
+    # FP64 sums of |Omega| U drift only at the level of FP32 rounding of
+    # the per-step change, far below the FP32 rounding of the state itself
+    tol = 1e-12 if precision == "fp32_flux" else 1e-10
+    assert abs(cons1[0] - cons0[0]) <= tol * abs(cons0[0])
+    assert abs(cons1[4] - cons0[4]) <= tol * abs(cons0[4])
