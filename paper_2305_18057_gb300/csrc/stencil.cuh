@@ -23,9 +23,17 @@
 
 #include "sensei_internal.cuh"
 
-#ifndef SENSEI_STENCIL_MIN_CTAS
-#define SENSEI_STENCIL_MIN_CTAS 2
-#endif
+// CTAs per SM the register allocation must allow: 2 for FP64 arithmetic
+// (the FP64 pipe is the bound; more warps cover its dependent latency), 3
+// for FP32 arithmetic (latency bound: more resident warps hide the loads).
+template <typename R>
+struct MinCtas {
+    static constexpr int value = 2;
+};
+template <>
+struct MinCtas<float> {
+    static constexpr int value = 3;
+};
 
 namespace sensei {
 
@@ -280,7 +288,7 @@ __device__ __forceinline__ void to_recon(const R q[NV], R gm1, int cons, bool in
 }
 
 template <typename R, typename TS, int LIM, bool TWO_D>
-__global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_kernel(const StencilParams<R> p)
+__global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(const StencilParams<R> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SL = SmemLayout<R>;
@@ -503,15 +511,36 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
             const long long mc = kpl + (long long)cj * p.ml.mpitch + ci;
             const long long rc = ((long long)k * p.nj + cj) * p.ni + ci;
             const long long nint = (long long)p.ni * p.nj * p.nk;
-            const double ivol = p.cm.ivol[mc];
-            const double vol = p.cm.vol[mc];
-            const double coef = -p.gdt * dt * ivol;
+            R rres[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 R rr = (sFi[v * FIV + tj * FIP + ti + 1] - sFi[v * FIV + tj * FIP + ti]) +
                        (sFj[v * FJV + (tj + 1) * FJP + ti] - sFj[v * FJV + tj * FJP + ti]);
                 if (!TWO_D) rr += Fkp[v] - Fkm[v];
-                double r = (double)rr;
+                rres[v] = rr;
+            }
+            if (p.mode == MODE_INCR && !p.partials) {
+                // FP32 increment only: no FP64 residual, no FP64 stage input
+                const float c32 = gdt_dt32 * p.cm.ivol32[mc];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    float delta = -c32 * (float)rres[v];
+                    if (p.dprev) delta = fmaf(beta32, p.dprev[cell + v * p.L.sv], delta);
+                    if (p.out) {
+                        p.out[cell + v * p.L.sv] = p.un[cell + v * p.L.sv] + (double)delta;
+                    } else {
+                        float xc = sizeof(TS) == 8 ? (float)in[cell + v * p.L.sv] : (float)p.un[cell + v * p.L.sv];
+                        p.dout[cell + v * p.L.sv] = delta;
+                        p.xout[cell + v * p.L.sv] = xc + delta;
+                    }
+                }
+            } else {
+            const double ivol = p.cm.ivol[mc];
+            const double vol = p.cm.vol[mc];
+            const double coef = -p.gdt * dt * ivol;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double r = (double)rres[v];
                 if (p.src) r -= p.src[v * nint + rc];
                 const double uin = (double)in[cell + v * p.L.sv];
                 if (p.mode == MODE_ACCUM) {
@@ -520,7 +549,7 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
                     p.out[cell + v * p.L.sv] = val;
                 } else if (p.mode == MODE_INCR) {
                     // FP32 increment; FP64 accumulation on the last stage
-                    float delta = -(gdt_dt32 * p.cm.ivol32[mc]) * (float)rr;
+                    float delta = -(gdt_dt32 * p.cm.ivol32[mc]) * (float)rres[v];
                     if (p.dprev) delta = fmaf(beta32, p.dprev[cell + v * p.L.sv], delta);
                     if (p.out) {
                         p.out[cell + v * p.L.sv] = p.un[cell + v * p.L.sv] + (double)delta;
@@ -539,6 +568,7 @@ __global__ void __launch_bounds__(NTHREADS, SENSEI_STENCIL_MIN_CTAS) stencil_ker
                     nmax[v] = fmax(nmax[v], fabs(r));
                     ncons[v] = fma(vol, uin, ncons[v]);
                 }
+            }
             }
         }
         if (!TWO_D) {
