@@ -35,6 +35,10 @@
  *   - Threading: a grid may be used by one host thread at a time.
  *   - Device: the grid belongs to the device that was current when it was
  *     created; later calls make that device current.
+ *   - Batching: a grid holds up to 256 blocks, all 2D or all 3D; every kernel
+ *     of a call covers all blocks in one launch.  Calls after sensei_set_bc
+ *     (or sensei_autotune) first upload the block table, which synchronises
+ *     the stream once.
  */
 #ifndef SENSEI_H
 #define SENSEI_H
@@ -189,6 +193,29 @@ sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double
  * SENSEI_ERR_NONPHYSICAL (and clears the flag) if a kernel met a
  * non-physical or non-finite state since the last call. */
 sensei_status sensei_norms(sensei_grid *grid, double *l2, double *linf, double *cons, sensei_stream stream);
+
+/* A CUDA graph of one sensei_rk_step (same arguments, fixed pointers),
+ * replayed by sensei_step_graph_launch on any stream.  With a captured step a
+ * whole SSPRK3 step of any number of blocks is one graph launch of six
+ * kernels: ghost fill, dt reduction, three persistent stencil launches,
+ * norm finalisation.  Creation synchronises `stream` and captures on a
+ * private stream (graph instantiation is done by the CUDA driver).  A graph
+ * refuses to launch (SENSEI_ERR_STATE) once boundary rules or the schedule of
+ * its grid have changed; make a new one then. */
+typedef struct sensei_step_graph sensei_step_graph;
+sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int rk, double cfl, double dt,
+                                       double *dt_used, sensei_stream stream, sensei_step_graph **out);
+sensei_status sensei_step_graph_launch(sensei_step_graph *graph, sensei_stream stream);
+sensei_status sensei_step_graph_destroy(sensei_step_graph *graph);
+
+/* Pick the work schedule of the persistent stencil launches by timing them
+ * on this grid and the states U (dt = 0 first-stage launches into the stage
+ * buffers; U's ghosts are refilled, its interior untouched): the k-extent of
+ * a work item (tile of 32 x 8 cells x kchunk planes) and persistent CTAs
+ * (resident CTAs x SMs, items taken round-robin) versus one CTA per item.
+ * Outputs (may be NULL) receive the choice.  Synchronises `stream`. */
+sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk, int *persistent,
+                              sensei_stream stream);
 
 /* Instrumentation (not part of the method).  While enabled (enable != 0),
  * every launch of the fused stencil kernel (the residual / Runge-Kutta stage

@@ -2,12 +2,20 @@
 //
 // The library allocates no device memory: every device array is either the
 // caller's (states, residuals, nodes, sources) or a slice of the caller's
-// workspace (metrics, Runge-Kutta stage buffers, reduction partials, the
-// time-step slot, the norms and the error word).
+// workspace (block descriptors, metrics, Runge-Kutta stage buffers, reduction
+// partials, the time-step slot, the norms and the error word).
+//
+// Every kernel of a step covers all blocks of the grid in one launch: the
+// ghost fill, the time-step reduction, one persistent stencil launch per RK
+// stage (which pushes the ghost layers of its output), the norm
+// finalisation.  The blocks' static descriptions live in a device table in
+// the workspace, refreshed from the host copy when boundary rules or the
+// schedule change.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "sensei_internal.cuh"
@@ -35,37 +43,27 @@ sensei_status fail(sensei_status st, const char *fmt, ...)
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
-struct Block {
-    int ni, nj, nk;
+// smallest k-chunk the schedule may use: sizes the per-item partials
+constexpr int KCHUNK_MIN = 4;
+constexpr int KCHUNK_CANDIDATES[] = {4, 8, 16, 32, 64, 128};
+
+struct HostBlock {
+    BlockDev dev;   // the image uploaded to the device table
     bool two_d;
-    StateLayout L;
-    MetricLayout ml;
-    double *fn[3][4];
-    float *fn32[3][4];
-    double *vol, *ivol;
-    float *ivol32;
-    double *sbar[3][4];
-    double *stage[2];       // FP64 stage states (FP64, FP32-flux)
-    float *xs[2], *ds[2];   // FP32 stage states and increments (FP32 storage)
-    int tiles_i, tiles_j, kchunk, nchunks;
-    long long part_off;   // first partial slot (CTA index) of this block
-    int nparts;
     bool bc_set[6];
-    int bc_type[6];
-    double bc_prim[6][NV];
-    int nbr[6], nbr_face[6];
 };
 
 // Byte offsets of every workspace slice, computed identically by
 // sensei_workspace_size and sensei_create_grid.
 struct Plan {
-    std::vector<Block> blocks;
-    size_t bytes = 0;
-    size_t off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0;
-    long long nparts = 0;
-    long long ncells = 0;
-    // per-block offsets (same order as the Block fields)
+    std::vector<HostBlock> blocks;
     std::vector<size_t> off_fn, off_fn32, off_vol, off_ivol, off_ivol32, off_sbar, off_stage;
+    size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0;
+    size_t bytes = 0;
+    long long max_items = 0;   // partial slots (items at the smallest k-chunk)
+    long long ncells = 0;
+    long long bc_total = 0;
+    bool two_d = false;
 };
 
 size_t take(size_t &cursor, size_t bytes)
@@ -89,21 +87,55 @@ sensei_status check_scheme(const sensei_scheme *s)
     return SENSEI_OK;
 }
 
+int chunks_for(int nk, bool two_d, int kchunk) { return two_d ? 1 : (nk + kchunk - 1) / kchunk; }
+
+long long bc_units(const HostBlock &H)
+{
+    long long u = 0;
+    const int nf = H.two_d ? 4 : 6;
+    for (int f = 0; f < nf; ++f) {
+        long long n1 = f < 2 ? H.dev.nj : H.dev.ni, n2 = f < 4 ? H.dev.nk : H.dev.nj;
+        u += n1 * n2 * 2;
+    }
+    return u;
+}
+
+// Item numbering (block-major) and ghost-fill unit numbering for a k-chunk;
+// returns the number of items.
+long long assign_items(std::vector<HostBlock> &blocks, int kchunk)
+{
+    long long items = 0, bc = 0;
+    for (HostBlock &H : blocks) {
+        BlockDev &B = H.dev;
+        B.kchunk = H.two_d ? 1 : std::min(kchunk, B.nk);
+        B.nchunks = chunks_for(B.nk, H.two_d, B.kchunk);
+        B.item0 = items;
+        items += (long long)B.tiles_i * B.tiles_j * B.nchunks;
+        B.bc0 = bc;
+        bc += bc_units(H);
+    }
+    return items;
+}
+
+long long total_items(const std::vector<HostBlock> &blocks)
+{
+    const BlockDev &L = blocks.back().dev;
+    return L.item0 + (long long)L.tiles_i * L.tiles_j * L.nchunks;
+}
+
 sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sensei_scheme *scheme, Plan &P)
 {
     if (!blocks || nblocks <= 0) return fail(SENSEI_ERR_INVALID_ARG, "need at least one block");
+    if (nblocks > MAX_BLOCKS) return fail(SENSEI_ERR_UNSUPPORTED, "at most %d blocks per grid", MAX_BLOCKS);
     sensei_status st = check_scheme(scheme);
     if (st != SENSEI_OK) return st;
     size_t cur = 0;
     P.blocks.resize(nblocks);
-    P.off_fn.resize(nblocks);
-    P.off_fn32.resize(nblocks);
-    P.off_vol.resize(nblocks);
-    P.off_ivol.resize(nblocks);
-    P.off_ivol32.resize(nblocks);
-    P.off_sbar.resize(nblocks);
-    P.off_stage.resize(nblocks);
+    for (auto *v : {&P.off_fn, &P.off_fn32, &P.off_vol, &P.off_ivol, &P.off_ivol32, &P.off_sbar, &P.off_stage})
+        v->resize(nblocks);
     const bool f32 = scheme->precision != SENSEI_FP64;
+    P.two_d = blocks[0].nk == 1;
+    long long tiles_total = 0;
     for (int b = 0; b < nblocks; ++b) {
         const sensei_block_desc &d = blocks[b];
         if (d.ni < 1 || d.nj < 1 || d.nk < 1)
@@ -111,13 +143,16 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
                         d.nk);
         if ((long long)d.ni * d.nj * d.nk > (1LL << 34))
             return fail(SENSEI_ERR_INVALID_ARG, "block %d: too many cells", b);
-        Block &B = P.blocks[b];
-        memset(&B, 0, sizeof B);
+        if ((d.nk == 1) != P.two_d)
+            return fail(SENSEI_ERR_INVALID_ARG, "block %d: 2D (nk == 1) and 3D blocks cannot share a grid", b);
+        HostBlock &H = P.blocks[b];
+        memset(&H, 0, sizeof H);
+        H.two_d = d.nk == 1;
+        BlockDev &B = H.dev;
         B.ni = d.ni;
         B.nj = d.nj;
         B.nk = d.nk;
-        B.two_d = d.nk == 1;
-        const int gk = B.two_d ? 0 : NG;
+        const int gk = H.two_d ? 0 : NG;
         const long long pitch = round_up(d.ni + 2 * NG, 4);
         B.L.sj = pitch;
         B.L.sk = pitch * (d.nj + 2 * NG);
@@ -130,21 +165,12 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         B.ml.mvolume = round_up(B.ml.mplane * (d.nk + 1), 32);
         B.tiles_i = (d.ni + TI - 1) / TI;
         B.tiles_j = (d.nj + TJ - 1) / TJ;
-        if (B.two_d) {
-            B.nchunks = 1;
-            B.kchunk = 1;
-        } else {
-            const long long target = 152LL * 8;
-            long long tiles = (long long)B.tiles_i * B.tiles_j;
-            long long nch = (target + tiles - 1) / tiles;
-            if (nch < 1) nch = 1;
-            if (nch > d.nk) nch = d.nk;
-            B.kchunk = (int)((d.nk + nch - 1) / nch);
-            B.nchunks = (d.nk + B.kchunk - 1) / B.kchunk;
+        for (int f = 0; f < 6; ++f) {
+            B.bc_type[f] = -1;
+            B.nbr[f] = -1;
+            B.nbr_face[f] = -1;
         }
-        B.nparts = B.tiles_i * B.tiles_j * B.nchunks;
-        B.part_off = P.nparts;
-        P.nparts += B.nparts;
+        tiles_total += (long long)B.tiles_i * B.tiles_j;
         P.ncells += (long long)d.ni * d.nj * d.nk;
         const size_t mv = (size_t)B.ml.mvolume;
         P.off_fn[b] = take(cur, 12 * mv * sizeof(double));
@@ -156,8 +182,18 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         // two FP64 stage states, or two FP32 stage states + two FP32 increments
         P.off_stage[b] = take(cur, 2 * (size_t)B.L.elems * sizeof(double));
     }
-    if (P.nparts > (1LL << 30)) return fail(SENSEI_ERR_INVALID_ARG, "grid too large");
-    P.off_partials = take(cur, (size_t)P.nparts * 3 * NV * sizeof(double));
+    // partial slots for the finest schedule
+    P.max_items = assign_items(P.blocks, KCHUNK_MIN);
+    P.bc_total = P.blocks.back().dev.bc0 + bc_units(P.blocks.back());
+    if (P.max_items > (1LL << 31)) return fail(SENSEI_ERR_INVALID_ARG, "grid too large");
+    // default schedule: about 8 items per SM of a 152-SM GB300
+    int max_nk = 1;
+    for (auto &H : P.blocks) max_nk = std::max(max_nk, H.dev.nk);
+    const long long nch = std::max(1LL, (152LL * 8 + tiles_total - 1) / tiles_total);
+    const int kchunk = (int)std::max<long long>(KCHUNK_MIN, (max_nk + nch - 1) / nch);
+    assign_items(P.blocks, kchunk);
+    P.off_desc = take(cur, (size_t)nblocks * sizeof(BlockDev));
+    P.off_partials = take(cur, (size_t)P.max_items * 3 * NV * sizeof(double));
     P.off_dtbits = take(cur, sizeof(unsigned long long));
     P.off_dtslot = take(cur, sizeof(double));
     P.off_norms = take(cur, 16 * sizeof(double));   // 15 norms + the error word
@@ -193,14 +229,20 @@ sensei_status sensei::fail_status(sensei_status st, const char *fmt, ...)
 
 struct sensei_grid {
     int device;
+    int sms;
     sensei_scheme scheme;
     Plan plan;
     char *ws;
+    BlockDev *desc;     // device table
     double *partials;
     unsigned long long *dt_bits;
     double *dt_slot;
-    double *norms;   // 15 doubles, then the error word
+    double *norms;      // 15 doubles, then the error word
     unsigned *err;
+    bool dirty = true;          // descriptors changed since the last upload
+    bool stage_ghosts = false;  // fixed (inflow) ghosts of the stage buffers set
+    int grid_mode = 0;          // 0: persistent (resident CTAs x SMs), 1: one CTA per item
+    int ctas_cache[3] = {0, 0, 0};
     // instrumentation
     bool prof = false;
     std::vector<cudaEvent_t> ev;   // start/end pairs
@@ -210,6 +252,11 @@ struct sensei_grid {
     {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
+};
+
+struct sensei_step_graph {
+    sensei_grid *grid;
+    cudaGraphExec_t exec;
 };
 
 namespace {
@@ -233,117 +280,129 @@ sensei_status check_states(const sensei_grid *g, double *const *U, const char *w
 sensei_status check_bcs(const sensei_grid *g)
 {
     for (size_t b = 0; b < g->plan.blocks.size(); ++b) {
-        const Block &B = g->plan.blocks[b];
-        for (int f = 0; f < (B.two_d ? 4 : 6); ++f)
-            if (!B.bc_set[f]) return fail(SENSEI_ERR_STATE, "block %zu face %d has no boundary condition", b, f);
+        const HostBlock &H = g->plan.blocks[b];
+        for (int f = 0; f < (H.two_d ? 4 : 6); ++f)
+            if (!H.bc_set[f]) return fail(SENSEI_ERR_STATE, "block %zu face %d has no boundary condition", b, f);
     }
     return SENSEI_OK;
 }
 
-CellMetrics cell_metrics(const Block &B)
+int precision_kind(const sensei_grid *g, bool in_f32)
 {
-    CellMetrics cm;
-    cm.vol = B.vol;
-    cm.ivol = B.ivol;
-    cm.ivol32 = B.ivol32;
-    for (int d = 0; d < 3; ++d)
-        for (int q = 0; q < 4; ++q) cm.sbar[d][q] = B.sbar[d][q];
-    return cm;
+    if (g->scheme.precision == SENSEI_FP64) return 0;
+    return in_f32 ? 2 : 1;
 }
 
-template <typename T>
-sensei_status fill_ghosts_impl(sensei_grid *g, T *const *U, cudaStream_t s)
+// persistent grid size of a stencil variant
+int stencil_grid(sensei_grid *g, int kind, long long nitems)
 {
-    const auto &blocks = g->plan.blocks;
-    for (size_t b = 0; b < blocks.size(); ++b) {
-        const Block &B = blocks[b];
-        BCParamsT<T> p;
-        memset(&p, 0, sizeof p);
-        p.ni = B.ni;
-        p.nj = B.nj;
-        p.nk = B.nk;
-        p.L = B.L;
-        p.U = U[b];
-        p.nfaces = B.two_d ? 4 : 6;
-        p.gamma = g->scheme.gamma;
-        p.ml = B.ml;
-        for (int fam = 0; fam < 3; ++fam)
-            for (int q = 0; q < 4; ++q) p.fm.n[fam][q] = B.fn[fam][q];
-        for (int f = 0; f < p.nfaces; ++f) {
-            FaceBC<T> &fb = p.f[f];
-            fb.type = B.bc_type[f];
-            memcpy(fb.prim, B.bc_prim[f], sizeof fb.prim);
-            long long n1 = f < 2 ? B.nj : B.ni;
-            long long n2 = f < 4 ? B.nk : B.nj;
-            p.count[f] = n1 * n2 * 2;
-            if (fb.type == SENSEI_BC_INTERFACE) {
-                const Block &N = blocks[B.nbr[f]];
-                fb.nbr = U[B.nbr[f]];
-                fb.nL = N.L;
-                fb.nni = N.ni;
-                fb.nnj = N.nj;
-                fb.nnk = N.nk;
-                fb.nbr_face = B.nbr_face[f];
-            }
-        }
-        CUDA_TRY(launch_bc(p, s));
-        g->kernel_launches++;
-    }
+    if (g->grid_mode == 1) return (int)std::min<long long>(nitems, (1LL << 31) - 1);
+    if (!g->ctas_cache[kind])
+        g->ctas_cache[kind] = std::max(1, stencil_ctas_per_sm(kind, g->scheme.limiter, g->plan.two_d));
+    return (int)std::min<long long>(nitems, (long long)g->ctas_cache[kind] * g->sms);
+}
+
+// Upload the descriptor table if boundary rules or the schedule changed.
+// Synchronises `s` (a pageable host-to-device copy); never inside a capture.
+sensei_status sync_descriptors(sensei_grid *g, cudaStream_t s)
+{
+    if (!g->dirty) return SENSEI_OK;
+    std::vector<BlockDev> tab(g->plan.blocks.size());
+    for (size_t b = 0; b < tab.size(); ++b) tab[b] = g->plan.blocks[b].dev;
+    CUDA_TRY(cudaMemcpyAsync(g->desc, tab.data(), tab.size() * sizeof(BlockDev), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    g->dirty = false;
     return SENSEI_OK;
 }
 
-const double RK_COEF[3][4][3] = {
-    // alpha, beta, gdt of out = alpha U^n + beta U^(s-1) - gdt dt R/|Omega|
-    {{0.0, 1.0, 1.0}, {0.5, 0.5, 0.5}},
-    {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}},
-    {{0.0, 1.0, 1.0 / 3.0}, {0.0, 1.0, 1.0 / 3.0}, {0.0, 1.0, 1.0 / 3.0}, {0.25, 0.75, 0.25}},
+sensei_status fill_slot(sensei_grid *g, int slot, double *const *U, cudaStream_t s)
+{
+    BCBatch p;
+    memset(&p, 0, sizeof p);
+    p.blocks = g->desc;
+    p.nblocks = (int)g->plan.blocks.size();
+    p.total = g->plan.bc_total;
+    p.slot = slot;
+    p.gamma = g->scheme.gamma;
+    if (U)
+        for (int b = 0; b < p.nblocks; ++b) p.user[b] = U[b];
+    CUDA_TRY(launch_bc(p, s));
+    g->kernel_launches++;
+    return SENSEI_OK;
+}
+
+struct StencilCall {
+    int mode;
+    int in_slot, out_slot, dprev, dout;
+    int push;
+    double alpha, beta, gdt;
+    const double *dt_slot;
+    double dt_scale;
+    bool partials;
+    double *const *user;
+    double *const *rout;
+    const double *const *src;
 };
-const int RK_STAGES[3] = {2, 3, 4};
 
 template <typename R>
-void fill_common(StencilParams<R> &p, const sensei_grid *g, const Block &B)
+void fill_params(BatchParams<R> &p, const sensei_grid *g, const StencilCall &c)
 {
-    p.ni = B.ni;
-    p.nj = B.nj;
-    p.nk = B.nk;
-    p.tiles_i = B.tiles_i;
-    p.tiles_j = B.tiles_j;
-    p.kchunk = B.kchunk;
-    p.nchunks = B.nchunks;
-    p.L = B.L;
-    p.cm = cell_metrics(B);
-    p.ml = B.ml;
+    memset(&p, 0, sizeof p);
+    const int nb = (int)g->plan.blocks.size();
+    p.blocks = g->desc;
+    p.nblocks = nb;
+    p.nitems = total_items(g->plan.blocks);
+    p.mode = c.mode;
+    p.in_slot = c.in_slot;
+    p.out_slot = c.out_slot;
+    p.dprev = c.dprev;
+    p.dout = c.dout;
+    p.push = c.push;
     p.gamma = (R)g->scheme.gamma;
     p.kappa = (R)g->scheme.kappa;
     p.eps = (R)g->scheme.eps;
     p.fix = (R)g->scheme.entropy_fix;
     p.cons = g->scheme.reconstruct_conserved ? 1 : 0;
+    p.alpha = c.alpha;
+    p.beta = c.beta;
+    p.gdt = c.gdt;
+    p.dt_slot = c.dt_slot;
+    p.dt_scale = c.dt_scale;
+    p.partials = c.partials ? g->partials : nullptr;
     p.err = g->err;
+    for (int b = 0; b < nb; ++b) {
+        p.user[b] = c.user ? c.user[b] : nullptr;
+        p.rout[b] = c.rout ? c.rout[b] : nullptr;
+        p.src[b] = c.src ? c.src[b] : nullptr;
+    }
 }
 
-struct StencilCall {
-    int mode;
-    const void *in;
-    bool in_f32;            // the stage input is an FP32 stage state
-    const double *un;
-    double *out;
-    const float *dprev;
-    float *dout, *xout;
-    double *Rout;
-    const double *src;
-    double alpha, beta, gdt;
-    const double *dt_slot;
-    double dt_scale;
-    bool partials;
-};
+sensei_status stencil_launch(sensei_grid *g, const StencilCall &c, cudaStream_t s)
+{
+    const bool in_f32 = c.in_slot == SLOT_X0 || c.in_slot == SLOT_X1;
+    const int kind = precision_kind(g, in_f32);
+    const long long nitems = total_items(g->plan.blocks);
+    const int grid = stencil_grid(g, kind, nitems);
+    if (kind == 0) {
+        BatchParams<double> p;
+        fill_params(p, g, c);
+        CUDA_TRY(launch_stencil_f64(p, g->scheme.limiter, g->plan.two_d, grid, s));
+    } else {
+        BatchParams<float> p;
+        fill_params(p, g, c);
+        if (kind == 2)
+            CUDA_TRY(launch_stencil_f32s(p, g->scheme.limiter, g->plan.two_d, grid, s));
+        else
+            CUDA_TRY(launch_stencil_f32(p, g->scheme.limiter, g->plan.two_d, grid, s));
+    }
+    return SENSEI_OK;
+}
 
-sensei_status stencil_launch(sensei_grid *g, const Block &B, const StencilCall &c, cudaStream_t s);
-
-sensei_status stencil(sensei_grid *g, const Block &B, const StencilCall &c, cudaStream_t s)
+sensei_status stencil(sensei_grid *g, const StencilCall &c, cudaStream_t s)
 {
     if (!g->prof) {
         g->kernel_launches++;
-        return stencil_launch(g, B, c, s);
+        return stencil_launch(g, c, s);
     }
     if (g->ev_used + 2 > g->ev.size()) {
         for (int n = 0; n < 2; ++n) {
@@ -355,7 +414,7 @@ sensei_status stencil(sensei_grid *g, const Block &B, const StencilCall &c, cuda
     cudaEvent_t e0 = g->ev[g->ev_used], e1 = g->ev[g->ev_used + 1];
     g->ev_used += 2;
     CUDA_TRY(cudaEventRecord(e0, s));
-    sensei_status st = stencil_launch(g, B, c, s);
+    sensei_status st = stencil_launch(g, c, s);
     if (st != SENSEI_OK) return st;
     CUDA_TRY(cudaEventRecord(e1, s));
     g->kernel_launches++;
@@ -363,53 +422,110 @@ sensei_status stencil(sensei_grid *g, const Block &B, const StencilCall &c, cuda
     return SENSEI_OK;
 }
 
-sensei_status stencil_launch(sensei_grid *g, const Block &B, const StencilCall &c, cudaStream_t s)
+const double RK_COEF[3][4][3] = {
+    // alpha, beta, gdt of U^(s) = alpha U^n + beta U^(s-1) - gdt dt R/|Omega|
+    {{0.0, 1.0, 1.0}, {0.5, 0.5, 0.5}},
+    {{0.0, 1.0, 1.0}, {0.75, 0.25, 0.25}, {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0}},
+    {{0.0, 1.0, 1.0 / 3.0}, {0.0, 1.0, 1.0 / 3.0}, {0.0, 1.0, 1.0 / 3.0}, {0.25, 0.75, 0.25}},
+};
+const int RK_STAGES[3] = {2, 3, 4};
+
+bool incr_mode(const sensei_grid *g) { return g->scheme.precision == SENSEI_FP32_STORE; }
+
+// Everything of a step that must not happen inside a stream capture: the
+// descriptor upload and the one-time ghost fill of the stage buffers (it
+// sets their fixed inflow ghosts; all other ghosts are pushed every stage).
+sensei_status prepare_step(sensei_grid *g, cudaStream_t s)
 {
-    if (g->scheme.precision == SENSEI_FP64) {
-        StencilParams<double> p;
-        memset(&p, 0, sizeof p);
-        fill_common(p, g, B);
-        for (int fam = 0; fam < 3; ++fam)
-            for (int q = 0; q < 4; ++q) p.fm.n[fam][q] = B.fn[fam][q];
-        p.mode = c.mode;
-        p.in = c.in;
-        p.un = c.un;
-        p.out = c.out;
-        p.Rout = c.Rout;
-        p.src = c.src;
-        p.alpha = c.alpha;
-        p.beta = c.beta;
-        p.gdt = c.gdt;
-        p.dt_slot = c.dt_slot;
-        p.dt_scale = c.dt_scale;
-        p.partials = c.partials ? g->partials + B.part_off * 3 * NV : nullptr;
-        CUDA_TRY(launch_stencil_f64(p, g->scheme.limiter, B.two_d, s));
-    } else {
-        StencilParams<float> p;
-        memset(&p, 0, sizeof p);
-        fill_common(p, g, B);
-        for (int fam = 0; fam < 3; ++fam)
-            for (int q = 0; q < 4; ++q) p.fm.n[fam][q] = B.fn32[fam][q];
-        p.mode = c.mode;
-        p.in = c.in;
-        p.un = c.un;
-        p.out = c.out;
-        p.dprev = c.dprev;
-        p.dout = c.dout;
-        p.xout = c.xout;
-        p.Rout = c.Rout;
-        p.src = c.src;
-        p.alpha = c.alpha;
-        p.beta = c.beta;
-        p.gdt = c.gdt;
-        p.dt_slot = c.dt_slot;
-        p.dt_scale = c.dt_scale;
-        p.partials = c.partials ? g->partials + B.part_off * 3 * NV : nullptr;
-        if (c.in_f32)
-            CUDA_TRY(launch_stencil_f32s(p, g->scheme.limiter, B.two_d, s));
-        else
-            CUDA_TRY(launch_stencil_f32(p, g->scheme.limiter, B.two_d, s));
+    sensei_status st = sync_descriptors(g, s);
+    if (st != SENSEI_OK) return st;
+    if (!g->stage_ghosts) {
+        const bool incr = incr_mode(g);
+        for (int n = 0; n < 2; ++n) {
+            st = fill_slot(g, incr ? SLOT_X0 + n : SLOT_ST0 + n, nullptr, s);
+            if (st != SENSEI_OK) return st;
+        }
+        g->stage_ghosts = true;
     }
+    return SENSEI_OK;
+}
+
+// One RK step, launches only (capturable once prepare_step has run).
+sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, double cfl, double dt, double *dt_used,
+                               cudaStream_t s)
+{
+    sensei_status st = fill_slot(grid, SLOT_USER, U, s);
+    if (st != SENSEI_OK) return st;
+    const double *dt_src;
+    double dt_scale;
+    const long long nitems = total_items(grid->plan.blocks);
+    if (cfl > 0.0) {
+        CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
+        CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, grid->dt_bits,
+                           grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms), s));
+        grid->kernel_launches++;
+        dt_src = (const double *)grid->dt_bits;
+        dt_scale = cfl;
+    } else {
+        CUDA_TRY(launch_set_scalar(grid->dt_slot, dt, s));
+        grid->kernel_launches++;
+        dt_src = grid->dt_slot;
+        dt_scale = 1.0;
+    }
+    if (dt_used) {
+        CUDA_TRY(launch_scale_copy(dt_used, dt_src, dt_scale, s));
+        grid->kernel_launches++;
+    }
+    const int S = RK_STAGES[rk];
+    const bool incr = incr_mode(grid);
+    for (int stage = 0; stage < S; ++stage) {
+        const double *co = RK_COEF[rk][stage];
+        const bool last = stage == S - 1;
+        StencilCall c;
+        memset(&c, 0, sizeof c);
+        c.alpha = co[0];
+        c.beta = co[1];
+        c.gdt = co[2];
+        c.dt_slot = dt_src;
+        c.dt_scale = dt_scale;
+        c.partials = stage == 0;
+        c.user = U;
+        c.push = 1;
+        c.dprev = -1;
+        c.dout = -1;
+        if (!incr) {
+            // FP64 stage states: U -> ST0 -> ST1 -> ST0 ... -> U
+            c.mode = MODE_ACCUM;
+            c.in_slot = stage == 0 ? SLOT_USER : SLOT_ST0 + (stage - 1) % 2;
+            c.out_slot = last ? SLOT_USER : SLOT_ST0 + stage % 2;
+        } else {
+            // FP32 storage: the first stage reads the FP64 master U, later
+            // stages the FP32 stage state X^(s-1); every stage but the last
+            // writes the FP32 increment D^(s) and X^(s); the last adds its
+            // increment to U in FP64
+            c.mode = MODE_INCR;
+            c.in_slot = stage == 0 ? SLOT_USER : SLOT_X0 + (stage - 1) % 2;
+            c.out_slot = last ? SLOT_USER : SLOT_X0 + stage % 2;
+            c.dprev = stage == 0 ? -1 : (stage - 1) % 2;
+            c.dout = last ? -1 : stage % 2;
+        }
+        st = stencil(grid, c, s);
+        if (st != SENSEI_OK) return st;
+    }
+    CUDA_TRY(launch_norms_finalize(grid->partials, (int)nitems, grid->plan.ncells, grid->norms, s));
+    grid->kernel_launches++;
+    return SENSEI_OK;
+}
+
+sensei_status check_step_args(sensei_grid *grid, double *const *U, int rk, double cfl, double dt)
+{
+    sensei_status st = check_grid(grid);
+    if (st == SENSEI_OK) st = check_states(grid, U, "U");
+    if (st == SENSEI_OK) st = check_bcs(grid);
+    if (st != SENSEI_OK) return st;
+    if (rk < SENSEI_RK2_SSP || rk > SENSEI_RK4_SSP2) return fail(SENSEI_ERR_INVALID_ARG, "unknown RK scheme %d", rk);
+    if (!(cfl > 0.0) && !(dt > 0.0 && dt < INFINITY))
+        return fail(SENSEI_ERR_INVALID_ARG, "need cfl > 0 or a finite dt > 0");
     return SENSEI_OK;
 }
 
@@ -483,56 +599,47 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
                     P.bytes);
     cudaStream_t s = (cudaStream_t)stream;
     sensei_grid *g = new sensei_grid();
-    if (cudaGetDevice(&g->device) != cudaSuccess) {
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
         delete g;
-        return fail(SENSEI_ERR_CUDA, "cudaGetDevice failed");
+        return fail(SENSEI_ERR_CUDA, "cannot query the current device");
     }
     g->scheme = *scheme;
     g->plan = P;
     g->ws = (char *)workspace;
+    g->desc = (BlockDev *)(g->ws + P.off_desc);
     g->partials = (double *)(g->ws + P.off_partials);
     g->dt_bits = (unsigned long long *)(g->ws + P.off_dtbits);
     g->dt_slot = (double *)(g->ws + P.off_dtslot);
     g->norms = (double *)(g->ws + P.off_norms);
     g->err = (unsigned *)(g->norms + 15);
     for (int b = 0; b < nblocks; ++b) {
-        Block &B = g->plan.blocks[b];
+        BlockDev &B = g->plan.blocks[b].dev;
         const size_t mv = (size_t)B.ml.mvolume;
-        double *fn = (double *)(g->ws + P.off_fn[b]);
-        float *fn32 = P.off_fn32[b] ? (float *)(g->ws + P.off_fn32[b]) : nullptr;
-        double *sb = (double *)(g->ws + P.off_sbar[b]);
-        for (int fam = 0; fam < 3; ++fam)
-            for (int q = 0; q < 4; ++q) {
-                B.fn[fam][q] = fn + (fam * 4 + q) * mv;
-                B.fn32[fam][q] = fn32 ? fn32 + (fam * 4 + q) * mv : nullptr;
-                B.sbar[fam][q] = sb + (fam * 4 + q) * mv;
-            }
-        B.vol = (double *)(g->ws + P.off_vol[b]);
-        B.ivol = (double *)(g->ws + P.off_ivol[b]);
-        B.ivol32 = P.off_ivol32[b] ? (float *)(g->ws + P.off_ivol32[b]) : nullptr;
-        B.stage[0] = (double *)(g->ws + P.off_stage[b]);
-        B.stage[1] = B.stage[0] + B.L.elems;
+        B.fn = (const double *)(g->ws + P.off_fn[b]);
+        B.fn32 = P.off_fn32[b] ? (const float *)(g->ws + P.off_fn32[b]) : nullptr;
+        B.vol = (const double *)(g->ws + P.off_vol[b]);
+        B.ivol = (const double *)(g->ws + P.off_ivol[b]);
+        B.ivol32 = P.off_ivol32[b] ? (const float *)(g->ws + P.off_ivol32[b]) : nullptr;
+        B.sbar = (const double *)(g->ws + P.off_sbar[b]);
+        B.st64[0] = (double *)(g->ws + P.off_stage[b]);
+        B.st64[1] = B.st64[0] + B.L.elems;
         // FP32 storage reuses the same bytes: X0, X1, D0, D1
-        B.xs[0] = (float *)B.stage[0];
+        B.xs[0] = (float *)B.st64[0];
         B.xs[1] = B.xs[0] + B.L.elems;
         B.ds[0] = B.xs[1] + B.L.elems;
         B.ds[1] = B.ds[0] + B.L.elems;
-        for (int f = 0; f < 6; ++f) {
-            B.bc_set[f] = false;
-            B.nbr[f] = -1;
-            B.nbr_face[f] = -1;
-        }
         MetricsOut mo;
         memset(&mo, 0, sizeof mo);
         for (int fam = 0; fam < 3; ++fam)
             for (int q = 0; q < 4; ++q) {
-                mo.n[fam][q] = B.fn[fam][q];
-                mo.n32[fam][q] = B.fn32[fam][q];
-                mo.sbar[fam][q] = B.sbar[fam][q];
+                mo.n[fam][q] = (double *)B.fn + (fam * 4 + q) * mv;
+                mo.n32[fam][q] = B.fn32 ? (float *)B.fn32 + (fam * 4 + q) * mv : nullptr;
+                mo.sbar[fam][q] = (double *)B.sbar + (fam * 4 + q) * mv;
             }
-        mo.vol = B.vol;
-        mo.ivol = B.ivol;
-        mo.ivol32 = B.ivol32;
+        mo.vol = (double *)B.vol;
+        mo.ivol = (double *)B.ivol;
+        mo.ivol32 = (float *)B.ivol32;
         cudaError_t e = launch_metrics(B.ni, B.nj, B.nk, nodes[b], mo, B.ml, s);
         if (e != cudaSuccess) {
             delete g;
@@ -563,7 +670,7 @@ sensei_status sensei_state_layout(const sensei_grid *grid, int block, sensei_lay
     if (!out) return fail(SENSEI_ERR_INVALID_ARG, "out is NULL");
     if (block < 0 || block >= (int)grid->plan.blocks.size())
         return fail(SENSEI_ERR_INVALID_ARG, "block %d out of range", block);
-    const Block &B = grid->plan.blocks[block];
+    const BlockDev &B = grid->plan.blocks[block].dev;
     out->stride_j = B.L.sj;
     out->stride_k = B.L.sk;
     out->stride_var = B.L.sv;
@@ -583,41 +690,43 @@ sensei_status sensei_set_bc(sensei_grid *grid, int block, int face, int type, co
     if (st != SENSEI_OK) return st;
     const int nb = (int)grid->plan.blocks.size();
     if (block < 0 || block >= nb) return fail(SENSEI_ERR_INVALID_ARG, "block %d out of range", block);
-    Block &B = grid->plan.blocks[block];
-    if (face < 0 || face >= (B.two_d ? 4 : 6))
-        return fail(SENSEI_ERR_INVALID_ARG, "face %d out of range for a %s block", face, B.two_d ? "2D" : "3D");
+    HostBlock &H = grid->plan.blocks[block];
+    BlockDev &B = H.dev;
+    if (face < 0 || face >= (H.two_d ? 4 : 6))
+        return fail(SENSEI_ERR_INVALID_ARG, "face %d out of range for a %s block", face, H.two_d ? "2D" : "3D");
     if (type < SENSEI_BC_PERIODIC || type > SENSEI_BC_INTERFACE)
         return fail(SENSEI_ERR_INVALID_ARG, "unknown boundary type %d", type);
+    const int axis = face >> 1;
+    const int n_own = axis == 0 ? B.ni : axis == 1 ? B.nj : B.nk;
+    // every rule reads or feeds the two cell layers next to a boundary
+    if (n_own < NG)
+        return fail(SENSEI_ERR_INVALID_ARG, "a block needs at least %d cells along a bounded direction (has %d)", NG,
+                    n_own);
     if (type == SENSEI_BC_INFLOW) {
         if (!prim) return fail(SENSEI_ERR_INVALID_ARG, "inflow needs the primitive state");
         if (!(prim[0] > 0.0) || !(prim[4] > 0.0))
             return fail(SENSEI_ERR_INVALID_ARG, "inflow state needs rho > 0 and p > 0");
         memcpy(B.bc_prim[face], prim, sizeof B.bc_prim[face]);
-    }
-    if (type == SENSEI_BC_INTERFACE) {
+    } else if (type == SENSEI_BC_INTERFACE) {
         if (orientation != 0) return fail(SENSEI_ERR_UNSUPPORTED, "only aligned interfaces (orientation 0)");
         if (nbr_block < 0 || nbr_block >= nb) return fail(SENSEI_ERR_INVALID_ARG, "neighbour block out of range");
-        const Block &N = grid->plan.blocks[nbr_block];
-        if (nbr_face < 0 || nbr_face >= (N.two_d ? 4 : 6) || (nbr_face >> 1) != (face >> 1) || nbr_face == face)
+        const HostBlock &NH = grid->plan.blocks[nbr_block];
+        const BlockDev &N = NH.dev;
+        if (nbr_face < 0 || nbr_face >= (NH.two_d ? 4 : 6) || (nbr_face >> 1) != axis || nbr_face == face)
             return fail(SENSEI_ERR_INVALID_ARG, "neighbour face must be the opposite side of the same direction");
-        if (N.two_d != B.two_d) return fail(SENSEI_ERR_INVALID_ARG, "cannot connect a 2D block to a 3D block");
         int a1 = face < 2 ? B.nj : B.ni, a2 = face < 4 ? B.nk : B.nj;
         int b1 = nbr_face < 2 ? N.nj : N.ni, b2 = nbr_face < 4 ? N.nk : N.nj;
         if (a1 != b1 || a2 != b2)
             return fail(SENSEI_ERR_INVALID_ARG, "interface faces differ in size (%d x %d vs %d x %d)", a1, a2, b1, b2);
-        const int axis = face >> 1;
         const int nb_n = axis == 0 ? N.ni : axis == 1 ? N.nj : N.nk;
         if (nb_n < NG) return fail(SENSEI_ERR_INVALID_ARG, "neighbour block too thin for two ghost layers");
         B.nbr[face] = nbr_block;
         B.nbr_face[face] = nbr_face;
-    } else if (type == SENSEI_BC_PERIODIC || type == SENSEI_BC_SLIP_WALL) {
-        // both rules read the two cells next to a boundary
-        const int axis = face >> 1;
-        const int n = axis == 0 ? B.ni : axis == 1 ? B.nj : B.nk;
-        if (n < NG) return fail(SENSEI_ERR_INVALID_ARG, "block too thin for this boundary rule (needs %d cells)", NG);
     }
     B.bc_type[face] = type;
-    B.bc_set[face] = true;
+    H.bc_set[face] = true;
+    grid->dirty = true;
+    grid->stage_ghosts = false;
     g_msg[0] = 0;
     return SENSEI_OK;
 }
@@ -630,7 +739,9 @@ sensei_status sensei_fill_ghosts(sensei_grid *grid, double *const *U, sensei_str
     if (st != SENSEI_OK) return st;
     Device dev;
     CUDA_TRY(dev.set(grid->device));
-    st = fill_ghosts_impl(grid, U, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = sync_descriptors(grid, s);
+    if (st == SENSEI_OK) st = fill_slot(grid, SLOT_USER, U, s);
     if (st == SENSEI_OK) g_msg[0] = 0;
     return st;
 }
@@ -646,21 +757,24 @@ sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const
     Device dev;
     CUDA_TRY(dev.set(grid->device));
     cudaStream_t s = (cudaStream_t)stream;
-    st = fill_ghosts_impl(grid, U, s);
+    st = sync_descriptors(grid, s);
+    if (st == SENSEI_OK) st = fill_slot(grid, SLOT_USER, U, s);
     if (st != SENSEI_OK) return st;
-    const auto &blocks = grid->plan.blocks;
-    for (size_t b = 0; b < blocks.size(); ++b) {
-        StencilCall c;
-        memset(&c, 0, sizeof c);
-        c.mode = MODE_RESIDUAL;
-        c.in = U[b];
-        c.Rout = R[b];
-        c.src = src ? src[b] : nullptr;
-        c.partials = true;
-        st = stencil(grid, blocks[b], c, s);
-        if (st != SENSEI_OK) return st;
-    }
-    CUDA_TRY(launch_norms_finalize(grid->partials, (int)grid->plan.nparts, grid->plan.ncells, grid->norms, s));
+    StencilCall c;
+    memset(&c, 0, sizeof c);
+    c.mode = MODE_RESIDUAL;
+    c.in_slot = SLOT_USER;
+    c.out_slot = SLOT_USER;
+    c.dprev = -1;
+    c.dout = -1;
+    c.partials = true;
+    c.user = U;
+    c.rout = R;
+    c.src = src;
+    st = stencil(grid, c, s);
+    if (st != SENSEI_OK) return st;
+    CUDA_TRY(launch_norms_finalize(grid->partials, (int)total_items(grid->plan.blocks), grid->plan.ncells,
+                                   grid->norms, s));
     grid->kernel_launches++;
     g_msg[0] = 0;
     return SENSEI_OK;
@@ -669,112 +783,158 @@ sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const
 sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double cfl, double dt, double *dt_used,
                              sensei_stream stream)
 {
+    sensei_status st = check_step_args(grid, U, rk, cfl, dt);
+    if (st != SENSEI_OK) return st;
+    Device dev;
+    CUDA_TRY(dev.set(grid->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    st = prepare_step(grid, s);
+    if (st == SENSEI_OK) st = rk_step_launches(grid, U, rk, cfl, dt, dt_used, s);
+    if (st == SENSEI_OK) g_msg[0] = 0;
+    return st;
+}
+
+sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int rk, double cfl, double dt,
+                                       double *dt_used, sensei_stream stream, sensei_step_graph **out)
+{
+    if (!out) return fail(SENSEI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    sensei_status st = check_step_args(grid, U, rk, cfl, dt);
+    if (st != SENSEI_OK) return st;
+    Device dev;
+    CUDA_TRY(dev.set(grid->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    st = prepare_step(grid, s);
+    if (st != SENSEI_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    // capture on a private stream: the caller's may be the legacy stream
+    cudaStream_t cs;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const bool prof = grid->prof;
+    grid->prof = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = rk_step_launches(grid, U, rk, cfl, dt, dt_used, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (st == SENSEI_OK && e2 != cudaSuccess) st = fail(SENSEI_ERR_CUDA, "capture: %s", cudaGetErrorString(e2));
+    } else {
+        st = fail(SENSEI_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    grid->prof = prof;
+    cudaStreamDestroy(cs);
+    if (st != SENSEI_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(SENSEI_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    sensei_step_graph *gr = new sensei_step_graph();
+    gr->grid = grid;
+    gr->exec = exec;
+    *out = gr;
+    g_msg[0] = 0;
+    return SENSEI_OK;
+}
+
+sensei_status sensei_step_graph_launch(sensei_step_graph *graph, sensei_stream stream)
+{
+    if (!graph) return fail(SENSEI_ERR_INVALID_ARG, "graph is NULL");
+    if (graph->grid->dirty || !graph->grid->stage_ghosts)
+        return fail(SENSEI_ERR_STATE, "the grid's boundary rules or schedule changed since the graph was made");
+    Device dev;
+    CUDA_TRY(dev.set(graph->grid->device));
+    CUDA_TRY(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+    return SENSEI_OK;
+}
+
+sensei_status sensei_step_graph_destroy(sensei_step_graph *graph)
+{
+    if (!graph) return fail(SENSEI_ERR_INVALID_ARG, "graph is NULL");
+    cudaGraphExecDestroy(graph->exec);
+    delete graph;
+    return SENSEI_OK;
+}
+
+sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk_out, int *persistent_out,
+                              sensei_stream stream)
+{
     sensei_status st = check_grid(grid);
     if (st == SENSEI_OK) st = check_states(grid, U, "U");
     if (st == SENSEI_OK) st = check_bcs(grid);
     if (st != SENSEI_OK) return st;
-    if (rk < SENSEI_RK2_SSP || rk > SENSEI_RK4_SSP2) return fail(SENSEI_ERR_INVALID_ARG, "unknown RK scheme %d", rk);
-    if (!(cfl > 0.0) && !(dt > 0.0 && dt < INFINITY))
-        return fail(SENSEI_ERR_INVALID_ARG, "need cfl > 0 or a finite dt > 0");
     Device dev;
     CUDA_TRY(dev.set(grid->device));
     cudaStream_t s = (cudaStream_t)stream;
-    const auto &blocks = grid->plan.blocks;
-    const int nb = (int)blocks.size();
-
-    st = fill_ghosts_impl(grid, U, s);
+    st = prepare_step(grid, s);
+    if (st == SENSEI_OK) st = fill_slot(grid, SLOT_USER, U, s);
     if (st != SENSEI_OK) return st;
-    const double *dt_src;
-    double dt_scale;
-    if (cfl > 0.0) {
-        CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
-        for (int b = 0; b < nb; ++b) {
-            const Block &B = blocks[b];
-            CUDA_TRY(launch_dt(B.ni, B.nj, B.nk, B.L, U[b], cell_metrics(B), B.ml, grid->scheme.gamma, grid->dt_bits,
-                               grid->err, s));
-            grid->kernel_launches++;
-        }
-        dt_src = (const double *)grid->dt_bits;
-        dt_scale = cfl;
-    } else {
-        CUDA_TRY(launch_set_scalar(grid->dt_slot, dt, s));
-        grid->kernel_launches++;
-        dt_src = grid->dt_slot;
-        dt_scale = 1.0;
-    }
-    if (dt_used) {
-        CUDA_TRY(launch_scale_copy(dt_used, dt_src, dt_scale, s));
-        grid->kernel_launches++;
-    }
-
-    const int S = RK_STAGES[rk];
-    const bool incr = grid->scheme.precision == SENSEI_FP32_STORE;
-    std::vector<double *> in(nb), outp(nb);
-    std::vector<float *> xin(nb);
-    for (int stage = 0; stage < S; ++stage) {
-        const double *co = RK_COEF[rk][stage];
-        const bool last = stage == S - 1;
-        if (!incr) {
-            // FP64 stage states: U -> st0 -> st1 -> ... -> U
-            for (int b = 0; b < nb; ++b) {
-                in[b] = stage == 0 ? U[b] : blocks[b].stage[(stage - 1) % 2];
-                outp[b] = last ? U[b] : blocks[b].stage[stage % 2];
+    // first-stage launches with dt = 0 into the stage buffers: they time the
+    // stencil without touching the caller's state
+    CUDA_TRY(launch_set_scalar(grid->dt_slot, 0.0, s));
+    const bool incr = incr_mode(grid);
+    StencilCall c;
+    memset(&c, 0, sizeof c);
+    c.mode = incr ? MODE_INCR : MODE_ACCUM;
+    c.in_slot = SLOT_USER;
+    c.out_slot = incr ? SLOT_X0 : SLOT_ST0;
+    c.dprev = -1;
+    c.dout = incr ? 0 : -1;
+    c.beta = 1.0;
+    c.gdt = 1.0;
+    c.dt_slot = grid->dt_slot;
+    c.dt_scale = 1.0;
+    c.user = U;
+    int max_nk = 1;
+    for (auto &H : grid->plan.blocks) max_nk = std::max(max_nk, H.dev.nk);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    const bool prof = grid->prof;
+    grid->prof = false;
+    float best = 1e30f;
+    int best_k = grid->plan.blocks[0].dev.kchunk, best_mode = grid->grid_mode;
+    for (int kc : KCHUNK_CANDIDATES) {
+        if (grid->plan.two_d && kc != KCHUNK_CANDIDATES[0]) continue;
+        if (kc > 2 * max_nk) continue;
+        assign_items(grid->plan.blocks, kc);
+        grid->dirty = true;
+        st = sync_descriptors(grid, s);
+        if (st != SENSEI_OK) break;
+        for (int mode = 0; mode < 2 && st == SENSEI_OK; ++mode) {
+            grid->grid_mode = mode;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3 && st == SENSEI_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                st = stencil_launch(grid, c, s);
+                cudaEventRecord(e1, s);
+                if (st == SENSEI_OK && cudaEventSynchronize(e1) != cudaSuccess)
+                    st = fail(SENSEI_ERR_CUDA, "autotune timing failed");
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms = std::min(ms, t);   // the first launch warms up
             }
-            if (stage > 0) {
-                st = fill_ghosts_impl(grid, in.data(), s);
-                if (st != SENSEI_OK) return st;
-            }
-            for (int b = 0; b < nb; ++b) {
-                StencilCall c;
-                memset(&c, 0, sizeof c);
-                c.mode = MODE_ACCUM;
-                c.in = in[b];
-                c.un = co[0] != 0.0 ? U[b] : nullptr;
-                c.out = outp[b];
-                c.alpha = co[0];
-                c.beta = co[1];
-                c.gdt = co[2];
-                c.dt_slot = dt_src;
-                c.dt_scale = dt_scale;
-                c.partials = stage == 0;
-                st = stencil(grid, blocks[b], c, s);
-                if (st != SENSEI_OK) return st;
-            }
-        } else {
-            // FP32 storage: the first stage reads the FP64 master U, later
-            // stages the FP32 stage state X^(s-1); every stage but the last
-            // writes the FP32 increment D^(s) and X^(s); the last adds its
-            // increment to U in FP64.
-            if (stage > 0) {
-                for (int b = 0; b < nb; ++b) xin[b] = blocks[b].xs[(stage - 1) % 2];
-                st = fill_ghosts_impl(grid, xin.data(), s);
-                if (st != SENSEI_OK) return st;
-            }
-            for (int b = 0; b < nb; ++b) {
-                const Block &B = blocks[b];
-                StencilCall c;
-                memset(&c, 0, sizeof c);
-                c.mode = MODE_INCR;
-                c.in = stage == 0 ? (const void *)U[b] : (const void *)B.xs[(stage - 1) % 2];
-                c.in_f32 = stage > 0;
-                c.un = U[b];
-                c.dprev = stage == 0 ? nullptr : B.ds[(stage - 1) % 2];
-                c.out = last ? U[b] : nullptr;
-                c.dout = last ? nullptr : B.ds[stage % 2];
-                c.xout = last ? nullptr : B.xs[stage % 2];
-                c.alpha = co[0];
-                c.beta = co[1];
-                c.gdt = co[2];
-                c.dt_slot = dt_src;
-                c.dt_scale = dt_scale;
-                c.partials = stage == 0;
-                st = stencil(grid, B, c, s);
-                if (st != SENSEI_OK) return st;
+            if (st == SENSEI_OK && ms < best) {
+                best = ms;
+                best_k = kc;
+                best_mode = mode;
             }
         }
+        if (st != SENSEI_OK) break;
     }
-    CUDA_TRY(launch_norms_finalize(grid->partials, (int)grid->plan.nparts, grid->plan.ncells, grid->norms, s));
-    grid->kernel_launches++;
+    grid->prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    assign_items(grid->plan.blocks, best_k);
+    grid->grid_mode = best_mode;
+    grid->dirty = true;
+    sensei_status st2 = sync_descriptors(grid, s);
+    if (st == SENSEI_OK) st = st2;
+    if (st != SENSEI_OK) return st;
+    if (kchunk_out) *kchunk_out = best_k;
+    if (persistent_out) *persistent_out = best_mode == 0;
     g_msg[0] = 0;
     return SENSEI_OK;
 }

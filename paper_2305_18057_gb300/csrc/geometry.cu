@@ -6,7 +6,7 @@
 // extrapolation on the GPU"), two layers per boundary face.
 #include <math.h>
 
-#include "sensei_internal.cuh"
+#include "blocks.cuh"
 
 namespace sensei {
 namespace {
@@ -116,95 +116,83 @@ __global__ void metrics_kernel(int ni, int nj, int nk, const double *__restrict_
 }
 
 // ------------------------------------------------------------------------
-// ghost cells
+// ghost cells: every boundary face of every block of one buffer slot
 // ------------------------------------------------------------------------
 
-__device__ __forceinline__ long long cell_at(const StateLayout &L, int i, int j, int k)
+template <typename T>
+__device__ __forceinline__ T *slot_buffer(const BlockDev &B, double *user, int slot);
+template <>
+__device__ __forceinline__ double *slot_buffer<double>(const BlockDev &B, double *user, int slot)
 {
-    return L.off + (long long)k * L.sk + (long long)j * L.sj + i;
+    return slot64(B, user, slot);
 }
-
-// ghost cell of face f, layer g (1 next to the boundary, 2 outer), and the
-// interior cell m cells inside the boundary (m = 0: the boundary cell)
-__device__ __forceinline__ void face_cells(int f, int ni, int nj, int nk, int t1, int t2, int g, int m, int &gi,
-                                           int &gj, int &gk_, int &mi, int &mj, int &mk)
+template <>
+__device__ __forceinline__ float *slot_buffer<float>(const BlockDev &B, double *, int slot)
 {
-    switch (f) {
-    case 0: gi = -g; gj = t1; gk_ = t2; mi = m; mj = t1; mk = t2; break;
-    case 1: gi = ni - 1 + g; gj = t1; gk_ = t2; mi = ni - 1 - m; mj = t1; mk = t2; break;
-    case 2: gi = t1; gj = -g; gk_ = t2; mi = t1; mj = m; mk = t2; break;
-    case 3: gi = t1; gj = nj - 1 + g; gk_ = t2; mi = t1; mj = nj - 1 - m; mk = t2; break;
-    case 4: gi = t1; gj = t2; gk_ = -g; mi = t1; mj = t2; mk = m; break;
-    default: gi = t1; gj = t2; gk_ = nk - 1 + g; mi = t1; mj = t2; mk = nk - 1 - m; break;
-    }
+    return slot32(B, slot);
 }
 
 template <typename T>
-__global__ void bc_kernel(BCParamsT<T> p)
+__global__ void bc_kernel(BCBatch p)
 {
-    long long total = 0;
-    for (int f = 0; f < p.nfaces; ++f) total += p.count[f];
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.total;
          t += (long long)gridDim.x * blockDim.x) {
+        const int b = find_block_bc(p.blocks, p.nblocks, t);
+        const BlockDev &B = p.blocks[b];
+        long long r = t - B.bc0;
+        const int nfaces = B.nk == 1 ? 4 : 6;
         int f = 0;
-        long long r = t;
-        while (r >= p.count[f]) {
-            r -= p.count[f];
+        while (f < nfaces - 1 && r >= face_units(B, f)) {
+            r -= face_units(B, f);
             ++f;
         }
-        int n1 = f < 2 ? p.nj : p.ni;
-        int layer = 1 + (int)(r % 2);
-        long long pos = r / 2;
-        int t1 = (int)(pos % n1);
-        int t2 = (int)(pos / n1);
-        const FaceBC<T> &bc = p.f[f];
-        int gi, gj, gk, mi, mj, mk;
+        const int n1 = f < 2 ? B.nj : B.ni;
+        const int layer = 1 + (int)(r % 2);
+        const long long pos = r / 2;
+        const int t1 = (int)(pos % n1);
+        const int t2 = (int)(pos / n1);
+        T *U = slot_buffer<T>(B, p.user[b], p.slot);
+        const int type = B.bc_type[f];
+        int gi, gj, gk, mi, mj, mk, a, bb, c;
+        face_cells(f, B.ni, B.nj, B.nk, t1, t2, layer, 0, gi, gj, gk, a, bb, c);
         T q[NV];
-        if (bc.type == SENSEI_BC_PERIODIC || bc.type == SENSEI_BC_SLIP_WALL) {
-            // periodic: the opposite face's layer-1 cell inside; wall: mirror
-            int src_face = bc.type == SENSEI_BC_PERIODIC ? (f ^ 1) : f;
-            int a, b, c;
-            face_cells(f, p.ni, p.nj, p.nk, t1, t2, layer, 0, gi, gj, gk, a, b, c);
-            face_cells(src_face, p.ni, p.nj, p.nk, t1, t2, 1, layer - 1, a, b, c, mi, mj, mk);
-            long long sc = cell_at(p.L, mi, mj, mk);
-            for (int v = 0; v < NV; ++v) q[v] = p.U[sc + v * p.L.sv];
-            if (bc.type == SENSEI_BC_SLIP_WALL) {
-                int fam = f >> 1;
-                int bi = mi, bj = mj, bk = mk;   // boundary face index: the cell's own minus face,
-                if (f == 1) bi = p.ni;           // or the block's plus face
-                if (f == 3) bj = p.nj;
-                if (f == 5) bk = p.nk;
-                if (f == 0) bi = 0;
-                if (f == 2) bj = 0;
-                if (f == 4) bk = 0;
-                long long fm = bk * p.ml.mplane + bj * p.ml.mpitch + bi;
-                const T nx = (T)p.fm.n[fam][0][fm], ny = (T)p.fm.n[fam][1][fm], nz = (T)p.fm.n[fam][2][fm];
-                const T mn = q[1] * nx + q[2] * ny + q[3] * nz;
-                q[1] -= T(2) * mn * nx;
-                q[2] -= T(2) * mn * ny;
-                q[3] -= T(2) * mn * nz;
+        if (type == SENSEI_BC_PERIODIC || type == SENSEI_BC_SLIP_WALL) {
+            // periodic: the opposite face's cell layer-1 inside; wall: the
+            // mirror image of the cell layer-1 inside this face
+            const int src_face = type == SENSEI_BC_PERIODIC ? (f ^ 1) : f;
+            face_cells(src_face, B.ni, B.nj, B.nk, t1, t2, 1, layer - 1, a, bb, c, mi, mj, mk);
+            const long long sc = cell_index(B.L, mi, mj, mk);
+            for (int v = 0; v < NV; ++v) q[v] = U[sc + v * B.L.sv];
+            if (type == SENSEI_BC_SLIP_WALL) {
+                double nx, ny, nz;
+                boundary_normal(B, f, t1, t2, nx, ny, nz);
+                const T tx = (T)nx, ty = (T)ny, tz = (T)nz;
+                const T mn = q[1] * tx + q[2] * ty + q[3] * tz;
+                q[1] -= T(2) * mn * tx;
+                q[2] -= T(2) * mn * ty;
+                q[3] -= T(2) * mn * tz;
             }
-        } else if (bc.type == SENSEI_BC_EXTRAPOLATE) {
-            face_cells(f, p.ni, p.nj, p.nk, t1, t2, layer, 0, gi, gj, gk, mi, mj, mk);
-            long long sc = cell_at(p.L, mi, mj, mk);
-            for (int v = 0; v < NV; ++v) q[v] = p.U[sc + v * p.L.sv];
-        } else if (bc.type == SENSEI_BC_INFLOW) {
-            face_cells(f, p.ni, p.nj, p.nk, t1, t2, layer, 0, gi, gj, gk, mi, mj, mk);
-            double rho = bc.prim[0], u = bc.prim[1], v = bc.prim[2], w = bc.prim[3], pr = bc.prim[4];
+        } else if (type == SENSEI_BC_EXTRAPOLATE) {
+            const long long sc = cell_index(B.L, a, bb, c);
+            for (int v = 0; v < NV; ++v) q[v] = U[sc + v * B.L.sv];
+        } else if (type == SENSEI_BC_INFLOW) {
+            const double *w = B.bc_prim[f];
+            const double rho = w[0], u = w[1], v = w[2], ww = w[3], pr = w[4];
             q[0] = (T)rho;
             q[1] = (T)(rho * u);
             q[2] = (T)(rho * v);
-            q[3] = (T)(rho * w);
-            q[4] = (T)(pr / (p.gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w));
-        } else {   // SENSEI_BC_INTERFACE: neighbour's layer-1 cell inside its face
-            int a, b, c;
-            face_cells(f, p.ni, p.nj, p.nk, t1, t2, layer, 0, gi, gj, gk, a, b, c);
-            face_cells(bc.nbr_face, bc.nni, bc.nnj, bc.nnk, t1, t2, 1, layer - 1, a, b, c, mi, mj, mk);
-            long long sc = cell_at(bc.nL, mi, mj, mk);
-            for (int v = 0; v < NV; ++v) q[v] = bc.nbr[sc + v * bc.nL.sv];
+            q[3] = (T)(rho * ww);
+            q[4] = (T)(pr / (p.gamma - 1.0) + 0.5 * rho * (u * u + v * v + ww * ww));
+        } else {   // SENSEI_BC_INTERFACE: the neighbour's cell layer-1 inside its face
+            const int nb = B.nbr[f];
+            const BlockDev &N = p.blocks[nb];
+            face_cells(B.nbr_face[f], N.ni, N.nj, N.nk, t1, t2, 1, layer - 1, a, bb, c, mi, mj, mk);
+            const T *NU = slot_buffer<T>(N, p.user[nb], p.slot);
+            const long long sc = cell_index(N.L, mi, mj, mk);
+            for (int v = 0; v < NV; ++v) q[v] = NU[sc + v * N.L.sv];
         }
-        long long gc = cell_at(p.L, gi, gj, gk);
-        for (int v = 0; v < NV; ++v) p.U[gc + v * p.L.sv] = q[v];
+        const long long gc = cell_index(B.L, gi, gj, gk);
+        for (int v = 0; v < NV; ++v) U[gc + v * B.L.sv] = q[v];
     }
 }
 
@@ -220,19 +208,16 @@ cudaError_t launch_metrics(int ni, int nj, int nk, const double *X, const Metric
     return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t launch_bc_t(const BCParamsT<T> &p, cudaStream_t s)
+cudaError_t launch_bc(const BCBatch &p, cudaStream_t s)
 {
-    long long total = 0;
-    for (int f = 0; f < p.nfaces; ++f) total += p.count[f];
-    if (total == 0) return cudaSuccess;
-    long long blocks = (total + 255) / 256;
+    if (p.total == 0) return cudaSuccess;
+    long long blocks = (p.total + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    bc_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(p);
+    if (p.slot == SLOT_X0 || p.slot == SLOT_X1)
+        bc_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(p);
+    else
+        bc_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
-
-cudaError_t launch_bc(const BCParamsT<double> &p, cudaStream_t s) { return launch_bc_t(p, s); }
-cudaError_t launch_bc(const BCParamsT<float> &p, cudaStream_t s) { return launch_bc_t(p, s); }
 
 }  // namespace sensei

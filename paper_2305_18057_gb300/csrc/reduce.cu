@@ -10,7 +10,7 @@
 // partials; one CTA sums them in a fixed order (deterministic).
 #include <math.h>
 
-#include "sensei_internal.cuh"
+#include "blocks.cuh"
 
 namespace sensei {
 namespace {
@@ -34,46 +34,64 @@ __device__ __forceinline__ double rsqrt_exact(double x)
     return y;
 }
 
-__global__ void dt_kernel(int ni, int nj, int nk, StateLayout L, const double *__restrict__ U, CellMetrics cm,
-                          MetricLayout ml, double gamma, unsigned long long *dt_bits, unsigned *err)
+struct DtUser {
+    double *u[MAX_BLOCKS];
+};
+
+// One CTA per work item (tile column x k-chunk of one block), grid-stride
+// over the items; each thread walks its column.
+__global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, int nblocks, long long nitems,
+                                                      const __grid_constant__ DtUser user, double gamma,
+                                                      unsigned long long *dt_bits, unsigned *err)
 {
-    const long long total = (long long)ni * nj * nk;
-    const int ndir = nk == 1 ? 2 : 3;
+    const int t = threadIdx.x;
+    const int ti = t % TI, tj = t / TI;
     double best = INFINITY;
     bool bad = false;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(t % ni);
-        int j = (int)((t / ni) % nj);
-        int k = (int)(t / ((long long)ni * nj));
-        const double *c = U + L.off + (long long)k * L.sk + (long long)j * L.sj + i;
-        double rho = c[0], mx = c[L.sv], my = c[2 * L.sv], mz = c[3 * L.sv], E = c[4 * L.sv];
-        double ir = rcp_exact(rho);
-        double u = mx * ir, v = my * ir, w = mz * ir;
-        double p = (gamma - 1.0) * (E - 0.5 * (mx * u + my * v + mz * w));
-        if (!(rho > 0.0 && p > 0.0 && rho < INFINITY && p < INFINITY)) {
-            bad = true;
-            continue;
+    for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int b = find_block_item(blocks, nblocks, item);
+        const BlockDev &B = blocks[b];
+        long long local = item - B.item0;
+        const int tile_i = (int)(local % B.tiles_i);
+        local /= B.tiles_i;
+        const int tile_j = (int)(local % B.tiles_j);
+        const int chunk = (int)(local / B.tiles_j);
+        const int i = tile_i * TI + ti, j = tile_j * TJ + tj;
+        if (i >= B.ni || j >= B.nj) continue;
+        const int k0 = chunk * B.kchunk, k1 = min(k0 + B.kchunk, B.nk);
+        const int ndir = B.nk == 1 ? 2 : 3;
+        const double *U = user.u[b];
+        const long long mv = B.ml.mvolume;
+        for (int k = k0; k < k1; ++k) {
+            const double *c = U + cell_index(B.L, i, j, k);
+            double rho = c[0], mx = c[B.L.sv], my = c[2 * B.L.sv], mz = c[3 * B.L.sv], E = c[4 * B.L.sv];
+            double ir = rcp_exact(rho);
+            double u = mx * ir, v = my * ir, w = mz * ir;
+            double p = (gamma - 1.0) * (E - 0.5 * (mx * u + my * v + mz * w));
+            if (!(rho > 0.0 && p > 0.0 && rho < INFINITY && p < INFINITY)) {
+                bad = true;
+                continue;
+            }
+            const double a2 = gamma * p * ir;
+            const double a = a2 * rsqrt_exact(a2);
+            const long long m = k * B.ml.mplane + j * B.ml.mpitch + i;
+            double sum = 0.0;
+            for (int d = 0; d < ndir; ++d) {
+                const double *sb = B.sbar + (long long)(d * 4) * mv;
+                double un = u * sb[m] + v * sb[mv + m] + w * sb[2 * mv + m];
+                sum += fabs(un) + a * sb[3 * mv + m];
+            }
+            best = fmin(best, B.vol[m] * rcp_exact(sum));
         }
-        const double a2 = gamma * p * ir;
-        double a = a2 * rsqrt_exact(a2);
-        long long m = k * ml.mplane + j * ml.mpitch + i;
-        double sum = 0.0;
-        for (int d = 0; d < ndir; ++d) {
-            double un = u * cm.sbar[d][0][m] + v * cm.sbar[d][1][m] + w * cm.sbar[d][2][m];
-            sum += fabs(un) + a * cm.sbar[d][3][m];
-        }
-        double loc = cm.vol[m] * rcp_exact(sum);
-        best = fmin(best, loc);
     }
     if (bad) atomicOr(err, ERR_NONPHYSICAL);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
-    __shared__ double red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __shared__ double red[NTHREADS / 32];
+    if ((t & 31) == 0) red[t >> 5] = best;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = fmin(best, red[w]);
+    if (t == 0) {
+        for (int w = 1; w < NTHREADS / 32; ++w) best = fmin(best, red[w]);
         if (best < INFINITY) atomicMin(dt_bits, (unsigned long long)__double_as_longlong(best));
     }
 }
@@ -106,14 +124,12 @@ __global__ void norms_finalize_kernel(const double *__restrict__ partials, int n
 
 }  // namespace
 
-cudaError_t launch_dt(int ni, int nj, int nk, const StateLayout &L, const double *U, const CellMetrics &cm,
-                      const MetricLayout &ml, double gamma, unsigned long long *dt_bits, unsigned *err,
-                      cudaStream_t s)
+cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
+                      unsigned long long *dt_bits, unsigned *err, int grid, cudaStream_t s)
 {
-    long long total = (long long)ni * nj * nk;
-    long long blocks = (total + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    dt_kernel<<<(unsigned)blocks, 256, 0, s>>>(ni, nj, nk, L, U, cm, ml, gamma, dt_bits, err);
+    DtUser u;
+    for (int b = 0; b < nblocks; ++b) u.u[b] = user[b];
+    dt_kernel<<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, dt_bits, err);
     return cudaGetLastError();
 }
 

@@ -63,6 +63,35 @@ struct MetricsOut {
 };
 
 // ------------------------------------------------------------------------
+// Batched launches.  Every kernel of a step covers all blocks of the grid in
+// one launch.  A block's static description lives in the workspace
+// (BlockDev); work items are (block, tile_i, tile_j, k-chunk) numbered
+// block-major, block b owning items [item0, item0 + tiles_i*tiles_j*nchunks).
+// ------------------------------------------------------------------------
+constexpr int MAX_BLOCKS = 256;
+
+// state buffer slots a launch reads or writes
+enum { SLOT_USER = 0, SLOT_ST0 = 1, SLOT_ST1 = 2, SLOT_X0 = 3, SLOT_X1 = 4 };
+
+struct BlockDev {
+    int ni, nj, nk;
+    StateLayout L;
+    MetricLayout ml;
+    const double *fn;       // face metrics: 12 arrays of mvolume, index (family*4 + q)
+    const float *fn32;      // their FP32 copies (null in FP64 mode)
+    const double *vol, *ivol;
+    const float *ivol32;
+    const double *sbar;     // spectral metrics: 12 arrays of mvolume, index (direction*4 + q)
+    double *st64[2];        // FP64 stage states
+    float *xs[2], *ds[2];   // FP32 stage states and increments
+    int tiles_i, tiles_j, kchunk, nchunks;
+    long long item0;        // first work item
+    long long bc0;          // first ghost-fill work unit
+    int bc_type[6], nbr[6], nbr_face[6];
+    double bc_prim[6][NV];
+};
+
+// ------------------------------------------------------------------------
 // Stencil launch modes:
 //   MODE_RESIDUAL  write R
 //   MODE_ACCUM     Runge-Kutta stage with an FP64 stage state:
@@ -70,81 +99,67 @@ struct MetricsOut {
 //   MODE_INCR      Runge-Kutta stage with FP32 stage storage: the FP32
 //                  increment D = U^(s) - U^n,
 //                    D = beta * Dprev - gdt * dt * ivol * R,
-//                  stored with the FP32 stage state X = float(U^n) + D
-//                  (dout, xout), or on the last stage accumulated in FP64,
-//                    out = Un + D.
-// The stage input `in` is FP64 (TS = double) or FP32 (TS = float) with the
-// element strides of StateLayout.
+//                  stored with the FP32 stage state X = float(U^n) + D, or on
+//                  the last stage accumulated in FP64, out = Un + D.
+// The stage input is FP64 (TS = double: the caller's U or an FP64 stage
+// state) or FP32 (TS = float: an FP32 stage state).  With push set, every
+// new cell value is also written into the ghost layers it feeds (the
+// neighbour's interface ghosts, the opposite periodic ghosts, the mirrored
+// wall ghosts, the extrapolation ghosts) of the same output slot, so the
+// next stage needs no separate ghost fill.
 // ------------------------------------------------------------------------
 enum { MODE_RESIDUAL = 0, MODE_ACCUM = 1, MODE_INCR = 2 };
 
 template <typename R>
-struct StencilParams {
-    int ni, nj, nk;
-    int tiles_i, tiles_j, kchunk, nchunks;
-    StateLayout L;
+struct BatchParams {
+    const BlockDev *blocks;
+    int nblocks;
+    long long nitems;
     int mode;
-    const void *in;         // stage input (ghosts filled), double or float
-    const double *un;       // U^n (null when not needed)
-    double *out;            // FP64 stage output
-    const float *dprev;     // MODE_INCR: previous increment (null on the first stage)
-    float *dout, *xout;     // MODE_INCR: increment and FP32 stage state (null on the last stage)
-    double *Rout;           // residual R[5][nk][nj][ni] (residual mode)
-    const double *src;      // |Omega| S_h, same layout as Rout (may be null)
-    FaceMetrics<R> fm;
-    CellMetrics cm;
-    MetricLayout ml;
+    int in_slot, out_slot;  // out_slot: SLOT_USER / SLOT_ST* (FP64) or SLOT_X* (FP32)
+    int dprev, dout;        // MODE_INCR: increment slots (0 or 1), -1 for none
+    int push;
     R gamma, kappa, eps, fix;
-    int cons;               // reconstruct conserved variables
+    int cons;
     double alpha, beta, gdt;
     const double *dt_slot;  // dt = dt_scale * *dt_slot
     double dt_scale;
-    double *partials;       // 15 doubles per CTA (null: no norms)
+    double *partials;       // 15 doubles per item (null: no norms)
     unsigned *err;
+    double *user[MAX_BLOCKS];        // the caller's U, per block
+    double *rout[MAX_BLOCKS];        // MODE_RESIDUAL: R[5][nk][nj][ni]
+    const double *src[MAX_BLOCKS];   // MODE_RESIDUAL: |Omega| S_h (or null)
 };
 
-// Boundary fill of one block: 6 faces; T = double (state) or float (FP32
-// stage state).
-template <typename T>
-struct FaceBC {
-    int type;
-    double prim[NV];
-    const T *nbr;           // neighbour block state (INTERFACE)
-    StateLayout nL;
-    int nni, nnj, nnk;      // neighbour dims
-    int nbr_face;
-};
-
-template <typename T>
-struct BCParamsT {
-    int ni, nj, nk;
-    StateLayout L;
-    T *U;
-    FaceBC<T> f[6];
-    int nfaces;             // 4 in 2D, 6 in 3D
-    long long count[6];     // work items per face (positions x layers)
+// Ghost fill of every boundary face of every block of one buffer slot.
+struct BCBatch {
+    const BlockDev *blocks;
+    int nblocks;
+    long long total;        // work units (positions x 2 layers over all faces)
+    int slot;               // SLOT_USER, SLOT_ST*, SLOT_X*
     double gamma;
-    FaceMetrics<double> fm;
-    MetricLayout ml;
+    double *user[MAX_BLOCKS];
 };
-using BCParams = BCParamsT<double>;
 
 // ------------------------------------------------------------------------
 // host-side launchers (defined in the .cu files)
 // ------------------------------------------------------------------------
 cudaError_t launch_metrics(int ni, int nj, int nk, const double *X, const MetricsOut &mo,
                            const MetricLayout &ml, cudaStream_t s);
-cudaError_t launch_bc(const BCParamsT<double> &p, cudaStream_t s);
-cudaError_t launch_bc(const BCParamsT<float> &p, cudaStream_t s);
+cudaError_t launch_bc(const BCBatch &p, cudaStream_t s);
 // FP64 arithmetic on an FP64 state
-cudaError_t launch_stencil_f64(const StencilParams<double> &p, int limiter, bool two_d, cudaStream_t s);
+cudaError_t launch_stencil_f64(const BatchParams<double> &p, int limiter, bool two_d, int grid, cudaStream_t s);
 // FP32 arithmetic on an FP64 state (FP32 flux; first FP32-storage stage; residuals)
-cudaError_t launch_stencil_f32(const StencilParams<float> &p, int limiter, bool two_d, cudaStream_t s);
+cudaError_t launch_stencil_f32(const BatchParams<float> &p, int limiter, bool two_d, int grid, cudaStream_t s);
 // FP32 arithmetic on an FP32 stage state
-cudaError_t launch_stencil_f32s(const StencilParams<float> &p, int limiter, bool two_d, cudaStream_t s);
-cudaError_t launch_dt(int ni, int nj, int nk, const StateLayout &L, const double *U, const CellMetrics &cm,
-                      const MetricLayout &ml, double gamma, unsigned long long *dt_bits, unsigned *err,
-                      cudaStream_t s);
+cudaError_t launch_stencil_f32s(const BatchParams<float> &p, int limiter, bool two_d, int grid, cudaStream_t s);
+// resident CTAs per SM of a stencil variant (0 on error); precision_kind
+// 0 = FP64, 1 = FP32 arithmetic on an FP64 state, 2 = on an FP32 state
+int stencil_ctas_per_sm(int precision_kind, int limiter, bool two_d);
+int stencil_ctas_per_sm_f32(int precision_kind, int limiter, bool two_d);
+int stencil_ctas_per_sm_f32s(int limiter, bool two_d);
+cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
+                      unsigned long long *dt_bits, unsigned *err, int grid, cudaStream_t s);
 cudaError_t launch_set_scalar(double *slot, double v, cudaStream_t s);
 cudaError_t launch_scale_copy(double *dst, const double *src, double scale, cudaStream_t s);
 // Record the thread-local message returned by sensei_last_error (api.cu).

@@ -21,7 +21,7 @@
 
 #include <math.h>
 
-#include "sensei_internal.cuh"
+#include "blocks.cuh"
 
 // CTAs per SM the register allocation must allow: 2 for FP64 arithmetic
 // (the FP64 pipe is the bound; more warps cover its dependent latency), 3
@@ -287,8 +287,92 @@ __device__ __forceinline__ void to_recon(const R q[NV], R gm1, int cons, bool in
     for (int v = 0; v < NV; ++v) out[v] = cons ? q[v] : w[v];
 }
 
+// Face metrics of one block in the arithmetic type R.
+template <typename R>
+__device__ __forceinline__ const R *face_metric_base(const BlockDev &B);
+template <>
+__device__ __forceinline__ const double *face_metric_base<double>(const BlockDev &B) { return B.fn; }
+template <>
+__device__ __forceinline__ const float *face_metric_base<float>(const BlockDev &B) { return B.fn32; }
+
+// The output buffer of a stage for block n: FP64 (the caller's U or an FP64
+// stage state) or FP32 (an FP32 stage state).
+template <typename T>
+__device__ __forceinline__ T *out_buffer(const BlockDev &N, double *user, int slot);
+template <>
+__device__ __forceinline__ double *out_buffer<double>(const BlockDev &N, double *user, int slot)
+{
+    return slot64(N, user, slot);
+}
+template <>
+__device__ __forceinline__ float *out_buffer<float>(const BlockDev &N, double *, int slot)
+{
+    return slot32(N, slot);
+}
+
+// Write the new value q of interior cell (i, j, k) of block b into every
+// ghost cell it feeds (the ghost rules of the boundary fill, applied from
+// the producing side): interface and periodic ghosts of layer m+1 for the
+// cell m cells inside a face, the mirrored wall ghost of layer m+1, both
+// extrapolation ghosts from the boundary cell.  Inflow ghosts are fixed.
+template <typename T, typename R>
+__device__ __noinline__ void push_ghosts(const BatchParams<R> &p, const BlockDev &B, int b, int i, int j, int k,
+                                         const T q[NV], int nfaces)
+{
+    for (int f = 0; f < nfaces; ++f) {
+        int m;
+        switch (f) {
+        case 0: m = i; break;
+        case 1: m = B.ni - 1 - i; break;
+        case 2: m = j; break;
+        case 3: m = B.nj - 1 - j; break;
+        case 4: m = k; break;
+        default: m = B.nk - 1 - k; break;
+        }
+        if (m > 1) continue;
+        const int type = B.bc_type[f];
+        if (type == SENSEI_BC_INFLOW || (type == SENSEI_BC_EXTRAPOLATE && m != 0)) continue;
+        int t1, t2;
+        tangential(f, i, j, k, t1, t2);
+        int gi, gj, gk, a, c, d;
+        if (type == SENSEI_BC_INTERFACE) {
+            const int nb = B.nbr[f];
+            const BlockDev &N = p.blocks[nb];
+            T *dst = out_buffer<T>(N, p.user[nb], p.out_slot);
+            face_cells(B.nbr_face[f], N.ni, N.nj, N.nk, t1, t2, m + 1, 0, gi, gj, gk, a, c, d);
+            const long long g = cell_index(N.L, gi, gj, gk);
+            for (int v = 0; v < NV; ++v) dst[g + v * N.L.sv] = q[v];
+            continue;
+        }
+        T *dst = out_buffer<T>(B, p.user[b], p.out_slot);
+        if (type == SENSEI_BC_PERIODIC) {
+            face_cells(f ^ 1, B.ni, B.nj, B.nk, t1, t2, m + 1, 0, gi, gj, gk, a, c, d);
+            const long long g = cell_index(B.L, gi, gj, gk);
+            for (int v = 0; v < NV; ++v) dst[g + v * B.L.sv] = q[v];
+        } else if (type == SENSEI_BC_EXTRAPOLATE) {
+            for (int layer = 1; layer <= 2; ++layer) {
+                face_cells(f, B.ni, B.nj, B.nk, t1, t2, layer, 0, gi, gj, gk, a, c, d);
+                const long long g = cell_index(B.L, gi, gj, gk);
+                for (int v = 0; v < NV; ++v) dst[g + v * B.L.sv] = q[v];
+            }
+        } else {   // slip wall: mirror image
+            double nx, ny, nz;
+            boundary_normal(B, f, t1, t2, nx, ny, nz);
+            const T tx = (T)nx, ty = (T)ny, tz = (T)nz;
+            const T mn = q[1] * tx + q[2] * ty + q[3] * tz;
+            face_cells(f, B.ni, B.nj, B.nk, t1, t2, m + 1, 0, gi, gj, gk, a, c, d);
+            const long long g = cell_index(B.L, gi, gj, gk);
+            dst[g] = q[0];
+            dst[g + B.L.sv] = q[1] - T(2) * mn * tx;
+            dst[g + 2 * B.L.sv] = q[2] - T(2) * mn * ty;
+            dst[g + 3 * B.L.sv] = q[3] - T(2) * mn * tz;
+            dst[g + 4 * B.L.sv] = q[4];
+        }
+    }
+}
+
 template <typename R, typename TS, int LIM, bool TWO_D>
-__global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(const StencilParams<R> p)
+__global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(const __grid_constant__ BatchParams<R> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SL = SmemLayout<R>;
@@ -298,6 +382,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     R *sFi = sPj + SL::PJ;
     R *sFj = sFi + SL::FI;
     double *sRed = reinterpret_cast<double *>(sFj + SL::FJ + ((SL::elems * sizeof(R)) % 8 ? 1 : 0));
+    __shared__ BlockDev sB;
 
     constexpr int WP = TI + 4;                 // sW row pitch
     constexpr int WPL = (TJ + 4) * WP;         // sW variable plane
@@ -306,19 +391,10 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     constexpr int PJP = TI, PJV = (TJ + 2) * PJP, PJS = NV * PJV;
     constexpr int FIP = TI + 1, FIV = TJ * FIP;
     constexpr int FJP = TI, FJV = (TJ + 1) * FJP;
+    constexpr int NFACES = TWO_D ? 4 : 6;
 
     const int t = threadIdx.x;
     const int ti = t % TI, tj = t / TI;
-    int item = blockIdx.x;
-    const int tile_i = item % p.tiles_i;
-    item /= p.tiles_i;
-    const int tile_j = item % p.tiles_j;
-    const int chunk = item / p.tiles_j;
-    const int i0 = tile_i * TI, j0 = tile_j * TJ;
-    const int k0 = TWO_D ? 0 : chunk * p.kchunk;
-    const int k1 = TWO_D ? 1 : min(k0 + p.kchunk, p.nk);
-    const int ci = i0 + ti, cj = j0 + tj;
-    const bool col_valid = ci < p.ni && cj < p.nj;
 
     const R gm1 = p.gamma - R(1);
     const R kg = p.gamma / gm1;
@@ -326,318 +402,398 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     const R c2 = p.eps * (R(1) + p.kappa) / R(4);
     const R half_eps = p.eps / R(2);
     const int cons = p.cons;
-
-    const TS *in = static_cast<const TS *>(p.in);
-    CellLoader<R, TS> ld{in, p.L, p.ni, p.nj, p.nk};
     const bool update = p.mode != MODE_RESIDUAL;
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
     const float gdt_dt32 = (float)(p.gdt * dt);   // MODE_INCR
     const float beta32 = (float)p.beta;
 
-    // per-thread FP64 norm accumulators (touched once per plane; under the
-    // 2-CTA register budget the compiler may keep them in local memory)
-    double nsq[NV], nmax[NV], ncons[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) nsq[v] = nmax[v] = ncons[v] = 0.0;
-
-    // per-thread k-window of the own column: centre plane, the two above,
-    // the plus-side k-state of the centre plane, the flux of its lower k-face
-    R Wc[NV], W1[NV], W2[NV], Pp[NV], Fkm[NV];
-    if (!TWO_D) {
-        R q[NV];
-        R Wm2[NV], Wm1[NV];
-        ld.raw(ci, cj, k0 - 2, q);
-        to_recon(q, gm1, cons, false, p.err, Wm2);
-        ld.raw(ci, cj, k0 - 1, q);
-        to_recon(q, gm1, cons, false, p.err, Wm1);
-        ld.raw(ci, cj, k0, q);
-        to_recon(q, gm1, cons, col_valid, p.err, Wc);
-        ld.raw(ci, cj, k0 + 1, q);
-        to_recon(q, gm1, cons, col_valid && k0 + 1 < p.nk, p.err, W1);
-        ld.raw(ci, cj, k0 + 2, q);
-        to_recon(q, gm1, cons, col_valid && k0 + 2 < p.nk, p.err, W2);
-        // face k0-1/2: left state from plane k0-1, right state from plane k0
-        R Lk[NV], Rk[NV], dummy;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            face_states<R, LIM>(Wm2[v], Wm1[v], Wc[v], c1, c2, half_eps, Lk[v], dummy);
-            face_states<R, LIM>(Wm1[v], Wc[v], W1[v], c1, c2, half_eps, Pp[v], Rk[v]);
-        }
-        long long fk = (long long)k0 * p.ml.mplane + (long long)min(cj, p.nj - 1) * p.ml.mpitch + min(ci, p.ni - 1);
-        face_flux(Lk, Rk, p.fm.n[2][0][fk], p.fm.n[2][1][fk], p.fm.n[2][2][fk], p.fm.n[2][3][fk], gm1, kg, p.fix,
-                  cons, Fkm);
-    }
-
-    for (int k = k0; k < k1; ++k) {
-        // ---- P0: the centre plane with its halo into shared memory
-        R pre[NV];
-        if (!TWO_D) {
-            ld.raw(ci, cj, k + 3, pre);   // prefetch the plane entering the window
-#pragma unroll
-            for (int v = 0; v < NV; ++v) W_at(v, tj, ti) = Wc[v];
-            // halo ring: 2 columns each side of the TJ rows, 2 rows each side of the TI columns
-            for (int e = t; e < 4 * TJ + 4 * TI; e += NTHREADS) {
-                int r, c;
-                if (e < 4 * TJ) {
-                    r = e >> 2;
-                    int s = e & 3;
-                    c = s < 2 ? s - 2 : TI + s - 2;
-                } else {
-                    int e2 = e - 4 * TJ;
-                    int s = e2 / TI;
-                    c = e2 % TI;
-                    r = s < 2 ? s - 2 : TJ + s - 2;
-                }
-                R q[NV];
-                R w[NV];
-                ld.raw(i0 + c, j0 + r, k, q);
-                to_recon(q, gm1, cons, false, p.err, w);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) W_at(v, r, c) = w[v];
-            }
-        } else {
-            for (int e = t; e < (TJ + 4) * (TI + 4); e += NTHREADS) {
-                int r = e / (TI + 4) - 2, c = e % (TI + 4) - 2;
-                bool corner = (r < 0 || r >= TJ) && (c < 0 || c >= TI);
-                if (corner) continue;
-                R q[NV];
-                R w[NV];
-                int gi = i0 + c, gj = j0 + r;
-                ld.raw(gi, gj, 0, q);
-                to_recon(q, gm1, cons, gi >= 0 && gi < p.ni && gj >= 0 && gj < p.nj && r >= 0 && r < TJ && c >= 0 &&
-                                           c < TI,
-                         p.err, w);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) W_at(v, r, c) = w[v];
-            }
+    // persistent: CTA x takes items x, x + grid, x + 2 grid, ...
+    for (long long item = blockIdx.x; item < p.nitems; item += gridDim.x) {
+        const int b = find_block_item(p.blocks, p.nblocks, item);
+        __syncthreads();   // the previous item is done with sB and the shared tiles
+        {
+            const int *src = reinterpret_cast<const int *>(&p.blocks[b]);
+            int *dst = reinterpret_cast<int *>(&sB);
+            for (int w = t; w < (int)(sizeof(BlockDev) / sizeof(int)); w += NTHREADS) dst[w] = src[w];
         }
         __syncthreads();
+        const BlockDev &B = sB;
+        long long local = item - B.item0;
+        const int tile_i = (int)(local % B.tiles_i);
+        local /= B.tiles_i;
+        const int tile_j = (int)(local % B.tiles_j);
+        const int chunk = (int)(local / B.tiles_j);
+        const int i0 = tile_i * TI, j0 = tile_j * TJ;
+        const int k0 = TWO_D ? 0 : chunk * B.kchunk;
+        const int k1 = TWO_D ? 1 : min(k0 + B.kchunk, B.nk);
+        const int ci = i0 + ti, cj = j0 + tj;
+        const bool col_valid = ci < B.ni && cj < B.nj;
+        const StateLayout L = B.L;
+        const MetricLayout ml = B.ml;
+        const R *fm = face_metric_base<R>(B);   // [family*4 + q][mvolume]
+        const TS *in = (p.in_slot == SLOT_X0 || p.in_slot == SLOT_X1)
+                           ? reinterpret_cast<const TS *>(slot32(B, p.in_slot))
+                           : reinterpret_cast<const TS *>(slot64(B, p.user[b], p.in_slot));
+        const double *un = p.user[b];
+        double *out64 = (p.mode != MODE_RESIDUAL && p.out_slot < SLOT_X0) ? slot64(B, p.user[b], p.out_slot) : nullptr;
+        float *xout = (p.mode == MODE_INCR && p.out_slot >= SLOT_X0) ? slot32(B, p.out_slot) : nullptr;
+        const float *dprev = p.dprev >= 0 ? B.ds[p.dprev] : nullptr;
+        float *dout = p.dout >= 0 ? B.ds[p.dout] : nullptr;
+        CellLoader<R, TS> ld{in, L, B.ni, B.nj, B.nk};
 
-        // ---- P1: face states, i direction (cells -1..TI of every row) and
-        //      j direction (rows -1..TJ of every column)
-        for (int e = t; e < TJ * (TI + 2) + (TJ + 2) * TI; e += NTHREADS) {
-            // the centre cell in sW, the stride to its neighbours along the
-            // direction, and where its two face states go
-            int wc, ws;
-            R *dst;
-            int dstride;
-            if (e < TJ * (TI + 2)) {
-                int r = e / (TI + 2), c = e % (TI + 2) - 1;
-                wc = (r + 2) * WP + (c + 2);
-                ws = 1;
-                dst = sPi + r * PIP + (c + 1);
-                dstride = PIV;
-            } else {
-                int e2 = e - TJ * (TI + 2);
-                int r = e2 / TI - 1, c = e2 % TI;
-                wc = (r + 2) * WP + (c + 2);
-                ws = WP;
-                dst = sPj + (r + 1) * PJP + c;
-                dstride = PJV;
-            }
-            const int side = dstride == PIV ? PIS : PJS;
+        // per-thread FP64 norm accumulators (touched once per plane; under
+        // the register budget the compiler may keep them in local memory)
+        double nsq[NV], nmax[NV], ncons[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const R *wv = sW + v * WPL + wc;
-                R pl, mn;
-                face_states<R, LIM>(wv[-ws], wv[0], wv[ws], c1, c2, half_eps, pl, mn);
-                dst[v * dstride] = pl;
-                dst[side + v * dstride] = mn;
-            }
-        }
-        __syncthreads();
+        for (int v = 0; v < NV; ++v) nsq[v] = nmax[v] = ncons[v] = 0.0;
 
-        // ---- P2: Roe flux of every i-face and j-face of the tile, once each
-        const long long kpl = (long long)k * p.ml.mplane;
-        for (int e = t; e < TJ * (TI + 1) + (TJ + 1) * TI; e += NTHREADS) {
-            R Lf[NV], Rf[NV], F[NV];
-            int fam, fi, fj;
-            R *dst;
-            if (e < TJ * (TI + 1)) {
-                int r = e / (TI + 1), c = e % (TI + 1);   // face between cells c-1 and c of row r
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    Lf[v] = sPi[v * PIV + r * PIP + c];
-                    Rf[v] = sPi[PIS + v * PIV + r * PIP + (c + 1)];
-                }
-                fam = 0;
-                fi = i0 + c;
-                fj = j0 + r;
-                dst = sFi + r * FIP + c;
-            } else {
-                int e2 = e - TJ * (TI + 1);
-                int r = e2 / TI, c = e2 % TI;              // face between rows r-1 and r of column c
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    Lf[v] = sPj[v * PJV + r * PJP + c];
-                    Rf[v] = sPj[PJS + v * PJV + (r + 1) * PJP + c];
-                }
-                fam = 1;
-                fi = i0 + c;
-                fj = j0 + r;
-                dst = sFj + r * FJP + c;
-            }
-            bool valid = fam == 0 ? (fi <= p.ni && fj < p.nj) : (fi < p.ni && fj <= p.nj);
-            R nx = R(1), ny = R(0), nz = R(0), A = R(0);
-            if (valid) {
-                long long m = kpl + (long long)fj * p.ml.mpitch + fi;
-                nx = p.fm.n[fam][0][m];
-                ny = p.fm.n[fam][1][m];
-                nz = p.fm.n[fam][2][m];
-                A = p.fm.n[fam][3][m];
-            }
-            face_flux(Lf, Rf, nx, ny, nz, A, gm1, kg, p.fix, cons, F);
-            const int vstride = fam == 0 ? FIV : FJV;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) dst[v * vstride] = F[v];
-        }
-        R Fkp[NV], Ppn[NV];
-        if (!TWO_D) {
-            // face k+1/2 of the own column: left = plus state of plane k,
-            // right = minus state of plane k+1
-            R Rk[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) face_states<R, LIM>(Wc[v], W1[v], W2[v], c1, c2, half_eps, Ppn[v], Rk[v]);
-            long long fk = (long long)(k + 1) * p.ml.mplane + (long long)min(cj, p.nj - 1) * p.ml.mpitch +
-                           min(ci, p.ni - 1);
-            face_flux(Pp, Rk, p.fm.n[2][0][fk], p.fm.n[2][1][fk], p.fm.n[2][2][fk], p.fm.n[2][3][fk], gm1, kg, p.fix,
-                      cons, Fkp);
-        }
-        __syncthreads();
-
-        // ---- P3: residual, update, norms
-        if (col_valid) {
-            const long long cell = p.L.off + (long long)k * p.L.sk + (long long)cj * p.L.sj + ci;
-            const long long mc = kpl + (long long)cj * p.ml.mpitch + ci;
-            const long long rc = ((long long)k * p.nj + cj) * p.ni + ci;
-            const long long nint = (long long)p.ni * p.nj * p.nk;
-            R rres[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                R rr = (sFi[v * FIV + tj * FIP + ti + 1] - sFi[v * FIV + tj * FIP + ti]) +
-                       (sFj[v * FJV + (tj + 1) * FJP + ti] - sFj[v * FJV + tj * FJP + ti]);
-                if (!TWO_D) rr += Fkp[v] - Fkm[v];
-                rres[v] = rr;
-            }
-            if (p.mode == MODE_INCR && !p.partials) {
-                // FP32 increment only: no FP64 residual, no FP64 stage input
-                const float c32 = gdt_dt32 * p.cm.ivol32[mc];
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    float delta = -c32 * (float)rres[v];
-                    if (p.dprev) delta = fmaf(beta32, p.dprev[cell + v * p.L.sv], delta);
-                    if (p.out) {
-                        p.out[cell + v * p.L.sv] = p.un[cell + v * p.L.sv] + (double)delta;
-                    } else {
-                        float xc = sizeof(TS) == 8 ? (float)in[cell + v * p.L.sv] : (float)p.un[cell + v * p.L.sv];
-                        p.dout[cell + v * p.L.sv] = delta;
-                        p.xout[cell + v * p.L.sv] = xc + delta;
-                    }
-                }
-            } else {
-            const double ivol = p.cm.ivol[mc];
-            const double vol = p.cm.vol[mc];
-            const double coef = -p.gdt * dt * ivol;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                double r = (double)rres[v];
-                if (p.src) r -= p.src[v * nint + rc];
-                const double uin = (double)in[cell + v * p.L.sv];
-                if (p.mode == MODE_ACCUM) {
-                    double val = p.beta * uin + coef * r;
-                    if (p.un) val += p.alpha * p.un[cell + v * p.L.sv];
-                    p.out[cell + v * p.L.sv] = val;
-                } else if (p.mode == MODE_INCR) {
-                    // FP32 increment; FP64 accumulation on the last stage
-                    float delta = -(gdt_dt32 * p.cm.ivol32[mc]) * (float)rres[v];
-                    if (p.dprev) delta = fmaf(beta32, p.dprev[cell + v * p.L.sv], delta);
-                    if (p.out) {
-                        p.out[cell + v * p.L.sv] = p.un[cell + v * p.L.sv] + (double)delta;
-                    } else {
-                        // the FP32 image of U^n: the loaded input on the
-                        // first stage, else rounded from the FP64 master
-                        float xc = sizeof(TS) == 8 ? (float)in[cell + v * p.L.sv] : (float)p.un[cell + v * p.L.sv];
-                        p.dout[cell + v * p.L.sv] = delta;
-                        p.xout[cell + v * p.L.sv] = xc + delta;
-                    }
-                } else {
-                    p.Rout[v * nint + rc] = r;
-                }
-                if (p.partials) {
-                    nsq[v] = fma(r, r, nsq[v]);
-                    nmax[v] = fmax(nmax[v], fabs(r));
-                    ncons[v] = fma(vol, uin, ncons[v]);
-                }
-            }
-            }
-        }
+        // per-thread k-window of the own column: centre plane, the two
+        // above, the plus-side k-state of the centre plane, the flux of its
+        // lower k-face
+        R Wc[NV], W1[NV], W2[NV], Pp[NV], Fkm[NV];
         if (!TWO_D) {
             R q[NV];
+            R Wm2[NV], Wm1[NV];
+            ld.raw(ci, cj, k0 - 2, q);
+            to_recon(q, gm1, cons, false, p.err, Wm2);
+            ld.raw(ci, cj, k0 - 1, q);
+            to_recon(q, gm1, cons, false, p.err, Wm1);
+            ld.raw(ci, cj, k0, q);
+            to_recon(q, gm1, cons, col_valid, p.err, Wc);
+            ld.raw(ci, cj, k0 + 1, q);
+            to_recon(q, gm1, cons, col_valid && k0 + 1 < B.nk, p.err, W1);
+            ld.raw(ci, cj, k0 + 2, q);
+            to_recon(q, gm1, cons, col_valid && k0 + 2 < B.nk, p.err, W2);
+            // face k0-1/2: left state from plane k0-1, right state from plane k0
+            R Lk[NV], Rk[NV], dummy;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                Fkm[v] = Fkp[v];
-                Pp[v] = Ppn[v];
-                Wc[v] = W1[v];
-                W1[v] = W2[v];
-                q[v] = pre[v];
+                face_states<R, LIM>(Wm2[v], Wm1[v], Wc[v], c1, c2, half_eps, Lk[v], dummy);
+                face_states<R, LIM>(Wm1[v], Wc[v], W1[v], c1, c2, half_eps, Pp[v], Rk[v]);
             }
-            to_recon(q, gm1, cons, col_valid && k + 3 < p.nk, p.err, W2);
+            const long long fk = (long long)k0 * ml.mplane + (long long)min(cj, B.nj - 1) * ml.mpitch + min(ci, B.ni - 1);
+            const R *f2 = fm + 8 * ml.mvolume;
+            face_flux(Lk, Rk, f2[fk], f2[ml.mvolume + fk], f2[2 * ml.mvolume + fk], f2[3 * ml.mvolume + fk], gm1, kg,
+                      p.fix, cons, Fkm);
         }
-    }
 
-    // ---- FP64 norm partials of this CTA, fixed-order reduction
-    if (p.partials) {
-        const int lane = t & 31, warp = t >> 5;
+        for (int k = k0; k < k1; ++k) {
+            // ---- P0: the centre plane with its halo into shared memory
+            R pre[NV];
+            if (!TWO_D) {
+                ld.raw(ci, cj, k + 3, pre);   // prefetch the plane entering the window
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            double a = nsq[v], b = nmax[v], c = ncons[v];
+                for (int v = 0; v < NV; ++v) W_at(v, tj, ti) = Wc[v];
+                // halo ring: 2 columns each side of the TJ rows, 2 rows each side of the TI columns
+                for (int e = t; e < 4 * TJ + 4 * TI; e += NTHREADS) {
+                    int r, c;
+                    if (e < 4 * TJ) {
+                        r = e >> 2;
+                        int sd = e & 3;
+                        c = sd < 2 ? sd - 2 : TI + sd - 2;
+                    } else {
+                        int e2 = e - 4 * TJ;
+                        int sd = e2 / TI;
+                        c = e2 % TI;
+                        r = sd < 2 ? sd - 2 : TJ + sd - 2;
+                    }
+                    R q[NV];
+                    R w[NV];
+                    ld.raw(i0 + c, j0 + r, k, q);
+                    to_recon(q, gm1, cons, false, p.err, w);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                a += __shfl_down_sync(0xffffffffu, a, o);
-                b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
-                c += __shfl_down_sync(0xffffffffu, c, o);
+                    for (int v = 0; v < NV; ++v) W_at(v, r, c) = w[v];
+                }
+            } else {
+                for (int e = t; e < (TJ + 4) * (TI + 4); e += NTHREADS) {
+                    int r = e / (TI + 4) - 2, c = e % (TI + 4) - 2;
+                    bool corner = (r < 0 || r >= TJ) && (c < 0 || c >= TI);
+                    if (corner) continue;
+                    R q[NV];
+                    R w[NV];
+                    int gi = i0 + c, gj = j0 + r;
+                    ld.raw(gi, gj, 0, q);
+                    to_recon(q, gm1, cons,
+                             gi >= 0 && gi < B.ni && gj >= 0 && gj < B.nj && r >= 0 && r < TJ && c >= 0 && c < TI,
+                             p.err, w);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) W_at(v, r, c) = w[v];
+                }
             }
-            if (lane == 0) {
-                sRed[(0 * NV + v) * (NTHREADS / 32) + warp] = a;
-                sRed[(1 * NV + v) * (NTHREADS / 32) + warp] = b;
-                sRed[(2 * NV + v) * (NTHREADS / 32) + warp] = c;
+            __syncthreads();
+
+            // ---- P1: face states, i direction (cells -1..TI of every row)
+            //      and j direction (rows -1..TJ of every column)
+            for (int e = t; e < TJ * (TI + 2) + (TJ + 2) * TI; e += NTHREADS) {
+                // the centre cell in sW, the stride to its neighbours along
+                // the direction, and where its two face states go
+                int wc, ws;
+                R *dst;
+                int dstride;
+                if (e < TJ * (TI + 2)) {
+                    int r = e / (TI + 2), c = e % (TI + 2) - 1;
+                    wc = (r + 2) * WP + (c + 2);
+                    ws = 1;
+                    dst = sPi + r * PIP + (c + 1);
+                    dstride = PIV;
+                } else {
+                    int e2 = e - TJ * (TI + 2);
+                    int r = e2 / TI - 1, c = e2 % TI;
+                    wc = (r + 2) * WP + (c + 2);
+                    ws = WP;
+                    dst = sPj + (r + 1) * PJP + c;
+                    dstride = PJV;
+                }
+                const int side = dstride == PIV ? PIS : PJS;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const R *wv = sW + v * WPL + wc;
+                    R pl, mn;
+                    face_states<R, LIM>(wv[-ws], wv[0], wv[ws], c1, c2, half_eps, pl, mn);
+                    dst[v * dstride] = pl;
+                    dst[side + v * dstride] = mn;
+                }
+            }
+            __syncthreads();
+
+            // ---- P2: Roe flux of every i-face and j-face of the tile, once each
+            const long long kpl = (long long)k * ml.mplane;
+            for (int e = t; e < TJ * (TI + 1) + (TJ + 1) * TI; e += NTHREADS) {
+                R Lf[NV], Rf[NV], F[NV];
+                int fam, fi, fj;
+                R *dst;
+                if (e < TJ * (TI + 1)) {
+                    int r = e / (TI + 1), c = e % (TI + 1);   // face between cells c-1 and c of row r
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        Lf[v] = sPi[v * PIV + r * PIP + c];
+                        Rf[v] = sPi[PIS + v * PIV + r * PIP + (c + 1)];
+                    }
+                    fam = 0;
+                    fi = i0 + c;
+                    fj = j0 + r;
+                    dst = sFi + r * FIP + c;
+                } else {
+                    int e2 = e - TJ * (TI + 1);
+                    int r = e2 / TI, c = e2 % TI;              // face between rows r-1 and r of column c
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        Lf[v] = sPj[v * PJV + r * PJP + c];
+                        Rf[v] = sPj[PJS + v * PJV + (r + 1) * PJP + c];
+                    }
+                    fam = 1;
+                    fi = i0 + c;
+                    fj = j0 + r;
+                    dst = sFj + r * FJP + c;
+                }
+                bool valid = fam == 0 ? (fi <= B.ni && fj < B.nj) : (fi < B.ni && fj <= B.nj);
+                R nx = R(1), ny = R(0), nz = R(0), A = R(0);
+                if (valid) {
+                    const R *fb = fm + (long long)(fam * 4) * ml.mvolume;
+                    const long long m = kpl + (long long)fj * ml.mpitch + fi;
+                    nx = fb[m];
+                    ny = fb[ml.mvolume + m];
+                    nz = fb[2 * ml.mvolume + m];
+                    A = fb[3 * ml.mvolume + m];
+                }
+                face_flux(Lf, Rf, nx, ny, nz, A, gm1, kg, p.fix, cons, F);
+                const int vstride = fam == 0 ? FIV : FJV;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) dst[v * vstride] = F[v];
+            }
+            R Fkp[NV], Ppn[NV];
+            if (!TWO_D) {
+                // face k+1/2 of the own column: left = plus state of plane k,
+                // right = minus state of plane k+1
+                R Rk[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) face_states<R, LIM>(Wc[v], W1[v], W2[v], c1, c2, half_eps, Ppn[v], Rk[v]);
+                const long long fk = (long long)(k + 1) * ml.mplane + (long long)min(cj, B.nj - 1) * ml.mpitch +
+                                     min(ci, B.ni - 1);
+                const R *f2 = fm + 8 * ml.mvolume;
+                face_flux(Pp, Rk, f2[fk], f2[ml.mvolume + fk], f2[2 * ml.mvolume + fk], f2[3 * ml.mvolume + fk], gm1,
+                          kg, p.fix, cons, Fkp);
+            }
+            __syncthreads();
+
+            // ---- P3: residual, update, ghost push, norms
+            if (col_valid) {
+                const long long cell = L.off + (long long)k * L.sk + (long long)cj * L.sj + ci;
+                const long long mc = kpl + (long long)cj * ml.mpitch + ci;
+                R rres[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    R rr = (sFi[v * FIV + tj * FIP + ti + 1] - sFi[v * FIV + tj * FIP + ti]) +
+                           (sFj[v * FJV + (tj + 1) * FJP + ti] - sFj[v * FJV + tj * FJP + ti]);
+                    if (!TWO_D) rr += Fkp[v] - Fkm[v];
+                    rres[v] = rr;
+                }
+                const bool boundary = ci < 2 || ci >= B.ni - 2 || cj < 2 || cj >= B.nj - 2 ||
+                                      (!TWO_D && (k < 2 || k >= B.nk - 2));
+                if (p.mode == MODE_INCR && !p.partials) {
+                    // FP32 increment only: no FP64 residual, no FP64 stage input
+                    const float c32 = gdt_dt32 * B.ivol32[mc];
+                    if (out64) {
+                        double q[NV];
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) {
+                            float delta = -c32 * (float)rres[v];
+                            if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
+                            q[v] = un[cell + v * L.sv] + (double)delta;
+                            out64[cell + v * L.sv] = q[v];
+                        }
+                        if (p.push && boundary) push_ghosts<double>(p, B, b, ci, cj, k, q, NFACES);
+                    } else {
+                        float q[NV];
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) {
+                            float delta = -c32 * (float)rres[v];
+                            if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
+                            const float xc = sizeof(TS) == 8 ? (float)in[cell + v * L.sv] : (float)un[cell + v * L.sv];
+                            dout[cell + v * L.sv] = delta;
+                            q[v] = xc + delta;
+                            xout[cell + v * L.sv] = q[v];
+                        }
+                        if (p.push && boundary) push_ghosts<float>(p, B, b, ci, cj, k, q, NFACES);
+                    }
+                } else {
+                    const double ivol = B.ivol[mc];
+                    const double vol = B.vol[mc];
+                    const double coef = -p.gdt * dt * ivol;
+                    const long long rc = ((long long)k * B.nj + cj) * B.ni + ci;
+                    const long long nint = (long long)B.ni * B.nj * B.nk;
+                    double q64[NV];
+                    float q32[NV];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        double r = (double)rres[v];
+                        if (p.mode == MODE_RESIDUAL && p.src[b]) r -= p.src[b][v * nint + rc];
+                        const double uin = (double)in[cell + v * L.sv];
+                        if (p.mode == MODE_ACCUM) {
+                            double val = p.beta * uin + coef * r;
+                            if (p.alpha != 0.0) val += p.alpha * un[cell + v * L.sv];
+                            out64[cell + v * L.sv] = val;
+                            q64[v] = val;
+                        } else if (p.mode == MODE_INCR) {
+                            // FP32 increment; FP64 accumulation on the last stage
+                            float delta = -(gdt_dt32 * B.ivol32[mc]) * (float)rres[v];
+                            if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
+                            if (out64) {
+                                q64[v] = un[cell + v * L.sv] + (double)delta;
+                                out64[cell + v * L.sv] = q64[v];
+                            } else {
+                                // the FP32 image of U^n: the loaded input on
+                                // the first stage, else rounded from the
+                                // FP64 master
+                                const float xc =
+                                    sizeof(TS) == 8 ? (float)in[cell + v * L.sv] : (float)un[cell + v * L.sv];
+                                dout[cell + v * L.sv] = delta;
+                                q32[v] = xc + delta;
+                                xout[cell + v * L.sv] = q32[v];
+                            }
+                        } else {
+                            p.rout[b][v * nint + rc] = r;
+                        }
+                        if (p.partials) {
+                            nsq[v] = fma(r, r, nsq[v]);
+                            nmax[v] = fmax(nmax[v], fabs(r));
+                            ncons[v] = fma(vol, uin, ncons[v]);
+                        }
+                    }
+                    if (p.push && boundary && p.mode != MODE_RESIDUAL) {
+                        if (out64)
+                            push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
+                        else
+                            push_ghosts<float>(p, B, b, ci, cj, k, q32, NFACES);
+                    }
+                }
+            }
+            if (!TWO_D) {
+                R q[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    Fkm[v] = Fkp[v];
+                    Pp[v] = Ppn[v];
+                    Wc[v] = W1[v];
+                    W1[v] = W2[v];
+                    q[v] = pre[v];
+                }
+                to_recon(q, gm1, cons, col_valid && k + 3 < B.nk, p.err, W2);
             }
         }
-        __syncthreads();
-        if (t < 3 * NV) {
-            int kind = t / NV;
-            double acc = 0.0;
-            for (int w = 0; w < NTHREADS / 32; ++w) {
-                double x = sRed[t * (NTHREADS / 32) + w];
-                acc = kind == 1 ? fmax(acc, x) : acc + x;
+
+        // ---- FP64 norm partials of this item, fixed-order reduction
+        if (p.partials) {
+            const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double a = nsq[v], bm = nmax[v], c = ncons[v];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_down_sync(0xffffffffu, a, o);
+                    bm = fmax(bm, __shfl_down_sync(0xffffffffu, bm, o));
+                    c += __shfl_down_sync(0xffffffffu, c, o);
+                }
+                if (lane == 0) {
+                    sRed[(0 * NV + v) * (NTHREADS / 32) + warp] = a;
+                    sRed[(1 * NV + v) * (NTHREADS / 32) + warp] = bm;
+                    sRed[(2 * NV + v) * (NTHREADS / 32) + warp] = c;
+                }
             }
-            p.partials[(long long)blockIdx.x * 3 * NV + t] = acc;
+            __syncthreads();
+            if (t < 3 * NV) {
+                const int kind = t / NV;
+                double acc = 0.0;
+                for (int w = 0; w < NTHREADS / 32; ++w) {
+                    double x = sRed[t * (NTHREADS / 32) + w];
+                    acc = kind == 1 ? fmax(acc, x) : acc + x;
+                }
+                p.partials[item * 3 * NV + t] = acc;
+            }
         }
     }
 }
 
 template <typename R, typename TS>
-cudaError_t launch_stencil_t(const StencilParams<R> &p, int limiter, bool two_d, cudaStream_t s)
-{
-    const size_t smem = SmemLayout<R>::bytes;
-    const unsigned grid = (unsigned)((long long)p.tiles_i * p.tiles_j * (two_d ? 1 : p.nchunks));
-    void (*fn)(const StencilParams<R>) = nullptr;
-#define SENSEI_PICK(L)                                                                                  \
-    fn = two_d ? stencil_kernel<R, TS, L, true> : stencil_kernel<R, TS, L, false>;
-    switch (limiter) {
-    case SENSEI_LIM_NONE: SENSEI_PICK(SENSEI_LIM_NONE); break;
-    case SENSEI_LIM_MINMOD: SENSEI_PICK(SENSEI_LIM_MINMOD); break;
-    default: SENSEI_PICK(SENSEI_LIM_VANLEER); break;
+struct StencilLauncher {
+    using Fn = void (*)(const BatchParams<R>);
+    static Fn pick(int limiter, bool two_d)
+    {
+        switch (limiter) {
+        case SENSEI_LIM_NONE: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_NONE, true>
+                                           : stencil_kernel<R, TS, SENSEI_LIM_NONE, false>;
+        case SENSEI_LIM_MINMOD: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_MINMOD, true>
+                                             : stencil_kernel<R, TS, SENSEI_LIM_MINMOD, false>;
+        default: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_VANLEER, true>
+                              : stencil_kernel<R, TS, SENSEI_LIM_VANLEER, false>;
+        }
     }
-#undef SENSEI_PICK
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    // all of the unified L1/shared storage as shared memory, so that the
-    // register-limited number of CTAs per SM is not cut by the carveout
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e != cudaSuccess) return e;
-    fn<<<grid, NTHREADS, smem, s>>>(p);
-    return cudaGetLastError();
-}
+    static cudaError_t prepare(Fn fn)
+    {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SmemLayout<R>::bytes);
+        if (e != cudaSuccess) return e;
+        // all of the unified L1/shared storage as shared memory, so that the
+        // register-limited number of CTAs per SM is not cut by the carveout
+        return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
+    static cudaError_t launch(const BatchParams<R> &p, int limiter, bool two_d, int grid, cudaStream_t s)
+    {
+        Fn fn = pick(limiter, two_d);
+        cudaError_t e = prepare(fn);
+        if (e != cudaSuccess) return e;
+        fn<<<grid, NTHREADS, SmemLayout<R>::bytes, s>>>(p);
+        return cudaGetLastError();
+    }
+    static int ctas_per_sm(int limiter, bool two_d)
+    {
+        Fn fn = pick(limiter, two_d);
+        if (prepare(fn) != cudaSuccess) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NTHREADS, SmemLayout<R>::bytes) != cudaSuccess)
+            return 0;
+        return n;
+    }
+};
 
 }  // namespace sensei

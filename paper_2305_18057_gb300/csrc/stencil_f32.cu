@@ -4,8 +4,14 @@
 #include "stencil.cuh"
 
 namespace sensei {
-cudaError_t launch_stencil_f32(const StencilParams<float> &p, int limiter, bool two_d, cudaStream_t s)
+cudaError_t launch_stencil_f32(const BatchParams<float> &p, int limiter, bool two_d, int grid, cudaStream_t s)
 {
-    return launch_stencil_t<float, double>(p, limiter, two_d, s);
+    return StencilLauncher<float, double>::launch(p, limiter, two_d, grid, s);
+}
+
+int stencil_ctas_per_sm_f32(int precision_kind, int limiter, bool two_d)
+{
+    if (precision_kind == 1) return StencilLauncher<float, double>::ctas_per_sm(limiter, two_d);
+    return stencil_ctas_per_sm_f32s(limiter, two_d);
 }
 }  // namespace sensei

@@ -4,8 +4,10 @@
 #include "stencil.cuh"
 
 namespace sensei {
-cudaError_t launch_stencil_f32s(const StencilParams<float> &p, int limiter, bool two_d, cudaStream_t s)
+cudaError_t launch_stencil_f32s(const BatchParams<float> &p, int limiter, bool two_d, int grid, cudaStream_t s)
 {
-    return launch_stencil_t<float, float>(p, limiter, two_d, s);
+    return StencilLauncher<float, float>::launch(p, limiter, two_d, grid, s);
 }
+
+int stencil_ctas_per_sm_f32s(int limiter, bool two_d) { return StencilLauncher<float, float>::ctas_per_sm(limiter, two_d); }
 }  // namespace sensei

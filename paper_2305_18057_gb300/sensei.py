@@ -29,6 +29,7 @@ NV = 5
 # every symbol include/sensei.h declares
 EXPORTS = ("sensei_workspace_size", "sensei_create_grid", "sensei_destroy_grid", "sensei_state_layout",
            "sensei_set_bc", "sensei_fill_ghosts", "sensei_residual", "sensei_rk_step", "sensei_norms",
+           "sensei_step_graph_create", "sensei_step_graph_launch", "sensei_step_graph_destroy", "sensei_autotune",
            "sensei_profile_enable", "sensei_profile_read", "sensei_residual_norms_noalloc", "sensei_last_error")
 
 
@@ -76,6 +77,11 @@ def load(path: str = LIB_PATH):
     L.sensei_residual.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]
     L.sensei_rk_step.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_double, C.c_double, vp, vp]
     L.sensei_norms.argtypes = [vp, dp, dp, dp, vp]
+    L.sensei_step_graph_create.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_double, C.c_double, vp, vp,
+                                           C.POINTER(vp)]
+    L.sensei_step_graph_launch.argtypes = [vp, vp]
+    L.sensei_step_graph_destroy.argtypes = [vp]
+    L.sensei_autotune.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
     L.sensei_profile_enable.argtypes = [vp, C.c_int]
     L.sensei_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
     L.sensei_residual_norms_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, dp, vp]
@@ -153,6 +159,28 @@ def sensei_norms(grid, stream_ptr, check=True):
     return st, np.array(l2[:]), np.array(linf[:]), np.array(cons[:])
 
 
+def sensei_step_graph_create(grid, U_ptrs, rk, cfl, dt, dt_used_ptr, stream_ptr):
+    out = C.c_void_p()
+    _check(load().sensei_step_graph_create(grid, _ptrs(U_ptrs), rk, cfl, dt, dt_used_ptr, stream_ptr,
+                                           C.byref(out)))
+    return out.value
+
+
+def sensei_step_graph_launch(graph, stream_ptr):
+    return _check(load().sensei_step_graph_launch(graph, stream_ptr))
+
+
+def sensei_step_graph_destroy(graph):
+    return _check(load().sensei_step_graph_destroy(graph))
+
+
+def sensei_autotune(grid, U_ptrs, stream_ptr):
+    """(kchunk, persistent) chosen by timing."""
+    k, p = C.c_int(), C.c_int()
+    _check(load().sensei_autotune(grid, _ptrs(U_ptrs), C.byref(k), C.byref(p), stream_ptr))
+    return k.value, bool(p.value)
+
+
 def sensei_profile_enable(grid, enable):
     return _check(load().sensei_profile_enable(grid, int(enable)))
 
@@ -178,6 +206,26 @@ def sensei_last_error() -> str:
 
 
 # ------------------------------------------------------------ convenience --
+
+class StepGraph:
+    def __init__(self, handle, grid):
+        self.handle = handle
+        self.grid = grid
+
+    def launch(self, stream=None):
+        sensei_step_graph_launch(self.handle, (stream or self.grid.stream).cuda_stream)
+
+    def close(self):
+        if self.handle:
+            sensei_step_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 class Grid:
     """A grid on the current CUDA device with its workspace and state tensors.
@@ -249,6 +297,15 @@ class Grid:
 
     def norms(self, check=True):
         return sensei_norms(self.handle, self.sptr, check=check)
+
+    def step_graph(self, Us, rk=RK3_SSP, cfl=0.5, dt=0.0, dt_used=None):
+        """A replayable CUDA graph of one rk_step on these states."""
+        h = sensei_step_graph_create(self.handle, [U.data_ptr() for U in Us], rk, cfl, dt,
+                                     dt_used.data_ptr() if dt_used is not None else None, self.sptr)
+        return StepGraph(h, self)
+
+    def autotune(self, Us):
+        return sensei_autotune(self.handle, [U.data_ptr() for U in Us], self.sptr)
 
     def profile(self, enable=True):
         sensei_profile_enable(self.handle, enable)

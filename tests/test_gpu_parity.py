@@ -139,3 +139,44 @@ def test_nonphysical_state_is_reported():
     g.rk_step(Us, RK["rk3"], dt=1e-6)
     st, *_ = g.norms(check=False)
     assert st == sensei.OK
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_step_graph_replays_eager_steps_bitwise(precision):
+    # a CUDA graph of one step (ghost fill, dt, three persistent stencil
+    # launches, norm finalisation) replayed on the lattice gives exactly the
+    # eagerly launched steps
+    w = CASES["lattice"]()
+    ga = gpu_grid(w, precision=precision)
+    Ua = gpu_states(ga, w)
+    gb = gpu_grid(w, precision=precision)
+    Ub = gpu_states(gb, w)
+    graph = gb.step_graph(Ub, RK["rk3"], cfl=0.5)
+    for _ in range(5):
+        ga.rk_step(Ua, RK["rk3"], cfl=0.5)
+        graph.launch()
+    torch.cuda.synchronize()
+    for b in range(len(w.dims)):
+        assert torch.equal(ga.interior_view(Ua[b], b), gb.interior_view(Ub[b], b)), b
+    graph.close()
+
+
+@pytest.mark.parametrize("case", ["periodic3d_odd", "lattice"])
+def test_autotuned_schedule_keeps_parity(case):
+    w = CASES[case]()
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    g = gpu_grid(w)
+    Us = gpu_states(g, w)
+    kchunk, persistent = g.autotune(Us)
+    assert kchunk in (4, 8, 16, 32, 64, 128)
+    # the autotuner's dt = 0 launches leave the interior untouched
+    for b in range(len(w.dims)):
+        np.testing.assert_array_equal(g.download(Us[b], b), w.U0[b])
+    dt_used = torch.zeros(1, dtype=torch.float64, device=Us[0].device)
+    for _ in range(20):
+        g.rk_step(Us, RK["rk3"], cfl=0.5, dt_used=dt_used)
+        og.rk_step(Uo, RK["rk3"], dt=dt_used.item())
+    torch.cuda.synchronize()
+    for b in range(len(w.dims)):
+        assert per_var_rel(g.download(Us[b], b), og.interior(Uo[b], b)) < 1e-9, b
