@@ -180,7 +180,8 @@ def make_workload(name, n=None):
     raise SystemExit(f"unknown workload {name}")
 
 
-def gpu_setup(w, precision):
+def gpu_setup(w, precision, tune=True):
+    """Grid, states and (tune) the autotuned schedule (kchunk, persistent)."""
     import torch
     from paper_2305_18057_gb300 import sensei, workloads as wl
     g = sensei.Grid(w.dims, w.nodes, gamma=w.gamma, limiter=wl.LIMITERS[w.limiter], kappa=w.kappa, eps=w.eps,
@@ -194,8 +195,26 @@ def gpu_setup(w, precision):
         U = g.new_state(b)
         g.upload(U, b, w.U0[b])
         Us.append(U)
+    schedule = g.autotune(Us) if tune else None
     torch.cuda.synchronize()
-    return g, Us
+    return g, Us, schedule
+
+
+def time_graph(g, Us, steps, rk, cfl):
+    """K replays of a CUDA graph of one step; returns ms."""
+    import torch
+    graph = g.step_graph(Us, rk, cfl=cfl)
+    graph.launch()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        graph.launch()
+    e1.record(s)
+    torch.cuda.synchronize()
+    graph.close()
+    return e0.elapsed_time(e1)
 
 
 def time_steps(g, Us, steps, rk, cfl, profile=False):
@@ -297,6 +316,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="grid size override (c3, c5): small profiling cases")
+    ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the step (default for c4)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -322,7 +342,11 @@ def main():
     cells = w.cells
     rk = sensei.RK3_SSP
     stages = 3
-    g, Us = gpu_setup(w, sensei.FP64)
+    # the batched multiblock workload runs FP32 flux on the FP64 state, as a
+    # CUDA graph per step; the others FP64 eagerly (mixed forms as variants)
+    main_prec = sensei.FP32_FLUX if args.workload == "c4" else sensei.FP64
+    use_graph = args.graph or args.workload == "c4"
+    g, Us, schedule = gpu_setup(w, main_prec)
     for _ in range(args.warmup):
         g.rk_step(Us, rk, cfl=w.cfl)
     torch.cuda.synchronize()
@@ -334,8 +358,15 @@ def main():
         dist.barrier()
     clocks.start()
     time.sleep(0.4)
-    ms, prof = time_steps(g, Us, args.steps, rk, w.cfl, profile=True)
-    clk = clocks.stop()
+    if use_graph:
+        ms = time_graph(g, Us, args.steps, rk, w.cfl)
+        clk = clocks.stop()
+        # kernel times for the roofline from an eager, instrumented pass
+        _, prof = time_steps(g, Us, max(3, min(args.steps, 5)), rk, w.cfl, profile=True)
+        prof = (prof[0], prof[1], prof[2] * args.steps // max(3, min(args.steps, 5)))
+    else:
+        ms, prof = time_steps(g, Us, args.steps, rk, w.cfl, profile=True)
+        clk = clocks.stop()
     units = cells * stages * args.steps
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -348,29 +379,39 @@ def main():
     # the dominant kernel: the fused stencil/update kernel
     st_ms, st_n, k_launches = prof
     per_launch_ms = st_ms / max(st_n, 1)
-    alpha_frac = 2.0 / 3.0   # SSPRK3: stages 2 and 3 blend U^n
-    flops = cells * (alg_flops_per_cell(w.limiter, two_d, False, True)
-                     + alg_flops_per_cell(w.limiter, two_d, True, False) * 2) / 3.0
-    byts = cells * sum(alg_bytes_per_cell("fp64", s_, two_d) for s_ in range(stages)) / stages
     peaks, peak_src = measured_peaks()
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    fp64_peak = fp64_peak_tflops(2070.0)
-    achieved_tf = flops / (per_launch_ms / 1e3) / 1e12
-    roofline = {
-        "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-        "frac": achieved_tf / fp64_peak, "traffic": None,
-        "kernel": "stencil_kernel<double> (fused MUSCL + Roe + residual + RK stage)",
-        "peak_source": "derived FP64 vector peak: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
-        "alg_flops_per_launch": flops, "kernel_ms_per_launch": per_launch_ms,
-        "hbm": {"achieved_gbs": byts / (per_launch_ms / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
-                "frac": byts / (per_launch_ms / 1e3) / 1e9 / peaks["hbm_gbs"], "peak_source": peak_src,
-                "alg_bytes_per_launch": byts},
-    }
+    form = "fp64" if main_prec == sensei.FP64 else "fp32_flux"
+    byts = cells * sum(alg_bytes_per_cell(form, s_, two_d) for s_ in range(stages)) / stages
+    hbm_gbs = byts / (per_launch_ms / 1e3) / 1e9
+    if main_prec == sensei.FP64:
+        flops = cells * (alg_flops_per_cell(w.limiter, two_d, False, True)
+                         + alg_flops_per_cell(w.limiter, two_d, True, False) * 2) / 3.0
+        fp64_peak = fp64_peak_tflops(2070.0)
+        achieved_tf = flops / (per_launch_ms / 1e3) / 1e12
+        roofline = {
+            "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved_tf / fp64_peak, "traffic": None,
+            "kernel": "stencil_kernel<double,double> (fused MUSCL + Roe + residual + RK stage)",
+            "peak_source": "derived FP64 vector peak: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
+            "alg_flops_per_launch": flops, "kernel_ms_per_launch": per_launch_ms,
+            "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_gbs / peaks["hbm_gbs"],
+                    "peak_source": peak_src, "alg_bytes_per_launch": byts},
+        }
+    else:
+        roofline = {
+            "bound": "hbm", "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src,
+            "kernel": "stencil_kernel<float,double> (FP32 MUSCL + Roe on the FP64 state, FP64 update)",
+            "alg_bytes_per_launch": byts, "kernel_ms_per_launch": per_launch_ms,
+        }
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": config_for(args.workload),
+        "dtype": "f64" if main_prec == sensei.FP64 else "f32 flux / f64 state", "data": "synthetic",
+        "config": dict(config_for(args.workload), cells=cells, blocks=len(w.dims),
+                       schedule={"kchunk": schedule[0], "persistent": schedule[1]},
+                       step="cuda graph per step" if use_graph else "eager launches"),
         "ssspnt": value * 1e-6, "gpu_launches": k_launches, "roofline": roofline, "clocks": clk,
     }
 
@@ -409,13 +450,16 @@ def main():
     # same state
     if not args.no_variants:
         n_cmp = args.warmup + args.steps
-        g64, U64 = gpu_setup(w, sensei.FP64)
+        g64, U64, _ = gpu_setup(w, sensei.FP64, tune=False)
         for _ in range(n_cmp):
             g64.rk_step(U64, rk, cfl=w.cfl)
         torch.cuda.synchronize()
         line["variants"] = {}
-        for vname, prec in (("fp32_flux", sensei.FP32_FLUX), ("fp32_store", sensei.FP32_STORE)):
-            gv, Uv = gpu_setup(w, prec)
+        for vname, prec in (("fp64", sensei.FP64), ("fp32_flux", sensei.FP32_FLUX),
+                            ("fp32_store", sensei.FP32_STORE)):
+            if prec == main_prec:
+                continue
+            gv, Uv, sched_v = gpu_setup(w, prec)
             for _ in range(args.warmup):
                 gv.rk_step(Uv, rk, cfl=w.cfl)
             msv, profv = time_steps(gv, Uv, args.steps, rk, w.cfl, profile=True)
@@ -431,7 +475,8 @@ def main():
             bv = cells * sum(alg_bytes_per_cell(vname, s_, two_d) for s_ in range(stages)) / stages
             line["variants"][vname] = {
                 "value": vv, "unit": UNIT, "ms_per_step": msv / args.steps,
-                "speedup_vs_fp64": vv / value if world == 1 else None,
+                "speedup_vs_fp64": (vv / value if main_prec == sensei.FP64 else None) if world == 1 else None,
+                "schedule": {"kchunk": sched_v[0], "persistent": sched_v[1]},
                 "rho_l2_rel_err_vs_fp64": rho_l2, "steps_compared": n_cmp,
                 "roofline": {"bound": "hbm", "achieved": bv / (stv / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": bv / (stv / 1e3) / 1e9 / peaks["hbm_gbs"],

@@ -120,6 +120,51 @@ __device__ __forceinline__ bool abs_le(float a, float b)
     return (__float_as_int(a) & 0x7fffffff) <= (__float_as_int(b) & 0x7fffffff);
 }
 
+// FP64 <-> FP32 conversions on the integer pipe, from the IEEE-754 binary64
+// and binary32 layouts: GB300 has 2 FP64 lanes per SM, so the conversion
+// instructions of the FP64 pipe would bound the FP32-arithmetic kernels.
+// double -> float: exponent rebiased by 1023 - 127, the top 23 fraction bits
+// kept and rounded by the next bit (ties away from zero; a carry into the
+// exponent is the correct result); values below the float normal range go
+// to +-0, above it to +-inf, NaN stays NaN.
+__device__ __forceinline__ float to_f32(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned frac = (unsigned)(b >> 29) & 0x7fffffu;
+    const unsigned rnd = (unsigned)(b >> 28) & 1u;
+    unsigned r = sign | ((unsigned)e << 23) | frac;
+    r += rnd;
+    const bool nan = ((hi >> 20) & 0x7ffu) == 0x7ffu && (b & 0xfffffffffffffULL) != 0;
+    r = e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u | (nan ? 0x400000u : 0u)) : r);
+    return __uint_as_float(r);
+}
+
+// float -> double, exact for normal floats (subnormals go to +-0)
+__device__ __forceinline__ double to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned m = u & 0x7fffffu;
+    const unsigned hi = e == 0u ? sign : (sign | ((e == 255u ? 0x7ffu : e + 896u) << 20) | (m >> 3));
+    const unsigned lo = e == 0u ? 0u : (m << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+template <typename To, typename From>
+__device__ __forceinline__ To cvt(From x);
+template <>
+__device__ __forceinline__ double cvt<double, double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float cvt<float, float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float cvt<float, double>(double x) { return to_f32(x); }
+template <>
+__device__ __forceinline__ double cvt<double, float>(float x) { return to_f64(x); }
+
 // conserved -> primitive; true if rho > 0, p > 0 and both finite
 template <typename R>
 __device__ __forceinline__ bool to_prim(const R q[NV], R gm1, R w[NV])
@@ -266,7 +311,7 @@ struct CellLoader {
         if (inside(i, j, k)) {
             const TS *c = in + L.off + (long long)k * L.sk + (long long)j * L.sj + i;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) q[v] = (R)__ldg(c + v * L.sv);
+            for (int v = 0; v < NV; ++v) q[v] = cvt<R, TS>(__ldg(c + v * L.sv));
         } else {   // outside the ghosted box: a harmless state, never used by a valid face
             q[0] = R(1);
             q[1] = q[2] = q[3] = R(0);
@@ -639,7 +684,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                         for (int v = 0; v < NV; ++v) {
                             float delta = -c32 * (float)rres[v];
                             if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
-                            q[v] = un[cell + v * L.sv] + (double)delta;
+                            q[v] = un[cell + v * L.sv] + to_f64(delta);
                             out64[cell + v * L.sv] = q[v];
                         }
                         if (p.push && boundary) push_ghosts<double>(p, B, b, ci, cj, k, q, NFACES);
@@ -649,7 +694,8 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                         for (int v = 0; v < NV; ++v) {
                             float delta = -c32 * (float)rres[v];
                             if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
-                            const float xc = sizeof(TS) == 8 ? (float)in[cell + v * L.sv] : (float)un[cell + v * L.sv];
+                            const float xc = sizeof(TS) == 8 ? cvt<float, TS>(in[cell + v * L.sv])
+                                                             : to_f32(un[cell + v * L.sv]);
                             dout[cell + v * L.sv] = delta;
                             q[v] = xc + delta;
                             xout[cell + v * L.sv] = q[v];
@@ -666,9 +712,9 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                     float q32[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        double r = (double)rres[v];
+                        double r = cvt<double, R>(rres[v]);
                         if (p.mode == MODE_RESIDUAL && p.src[b]) r -= p.src[b][v * nint + rc];
-                        const double uin = (double)in[cell + v * L.sv];
+                        const double uin = cvt<double, TS>(in[cell + v * L.sv]);
                         if (p.mode == MODE_ACCUM) {
                             double val = p.beta * uin + coef * r;
                             if (p.alpha != 0.0) val += p.alpha * un[cell + v * L.sv];
@@ -679,14 +725,14 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                             float delta = -(gdt_dt32 * B.ivol32[mc]) * (float)rres[v];
                             if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
                             if (out64) {
-                                q64[v] = un[cell + v * L.sv] + (double)delta;
+                                q64[v] = un[cell + v * L.sv] + to_f64(delta);
                                 out64[cell + v * L.sv] = q64[v];
                             } else {
                                 // the FP32 image of U^n: the loaded input on
                                 // the first stage, else rounded from the
                                 // FP64 master
-                                const float xc =
-                                    sizeof(TS) == 8 ? (float)in[cell + v * L.sv] : (float)un[cell + v * L.sv];
+                                const float xc = sizeof(TS) == 8 ? cvt<float, TS>(in[cell + v * L.sv])
+                                                                 : to_f32(un[cell + v * L.sv]);
                                 dout[cell + v * L.sv] = delta;
                                 q32[v] = xc + delta;
                                 xout[cell + v * L.sv] = q32[v];
