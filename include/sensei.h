@@ -185,6 +185,16 @@ sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const
 sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double cfl, double dt,
                              double *dt_used, sensei_stream stream);
 
+/* One step with local time stepping, for marching to a steady state (the
+ * paper's inlet case is steady): every cell advances by its own step
+ * dt_c = cfl |Omega_c| / sum_d (|u . Sbar_d| + c |Sbar_d|), evaluated on U^n
+ * and frozen over the stages (the spectral-radius bound of sensei_rk_step,
+ * without the minimum over cells).  Not time-accurate; the steady state
+ * R(U) = 0 is the same.  dt_min (device, 1 double, may be NULL) receives the
+ * smallest dt_c.  Norms as for sensei_rk_step; watch their decay. */
+sensei_status sensei_rk_step_local(sensei_grid *grid, double *const *U, int rk, double cfl, double *dt_min,
+                                   sensei_stream stream);
+
 /* Synchronise `stream` and copy out (host arrays of 5 doubles, any may be
  * NULL) the norms recorded by the last sensei_residual or sensei_rk_step:
  *   l2[q] = sqrt(sum_c R_q^2 / N), linf[q] = max_c |R_q|, cons[q] = sum_c |Omega_c| U_q

@@ -73,6 +73,8 @@ def lib():
             L.ora_rk_step.restype = C.c_double
             L.ora_rk_step.argtypes = [C.c_void_p, C.POINTER(_dp), C.POINTER(_dp), C.c_int,
                                       C.c_double, C.c_double, _dp]
+            L.ora_rk_step_local.restype = C.c_double
+            L.ora_rk_step_local.argtypes = [C.c_void_p, C.POINTER(_dp), C.POINTER(_dp), C.c_int, C.c_double, _dp]
             L.ora_rk_tableau.argtypes = [C.c_int, _dp, _dp, C.POINTER(C.c_int)]
             L.ora_euler_flux.argtypes = [C.c_double, _dp, _dp, _dp]
             L.ora_roe_flux.argtypes = [C.c_double, C.c_double, _dp, _dp, _dp, _dp]
@@ -239,6 +241,14 @@ class OracleGrid:
         out = np.zeros(15)
         lib().ora_norms(self._h, _ptrs(Rs), _ptrs(Us), _ptr(out))
         return out[:5].copy(), out[5:10].copy(), out[10:].copy()
+
+    def rk_step_local(self, Us, rk=RK3_SSP, cfl=0.5, src=None):
+        """One step with local time stepping (every cell its own dt); returns
+        (smallest dt, norms)."""
+        out = np.zeros(15)
+        srcp = _ptrs(src) if src is not None else None
+        dt_min = lib().ora_rk_step_local(self._h, _ptrs(Us), srcp, rk, cfl, _ptr(out))
+        return dt_min, (out[:5].copy(), out[5:10].copy(), out[10:].copy())
 
     def rk_step(self, Us, rk=RK3_SSP, cfl=0.5, dt=0.0, src=None):
         """One Runge-Kutta step in place; returns (dt_used, (l2, linf, cons))."""

@@ -822,6 +822,43 @@ void ora_norms(const ora_grid *g, double *const *R, double *const *U, double *ou
     }
 }
 
+/* local time step of one cell: cfl * |Omega| / sum_d (|u . Sbar_d| + c |Sbar_d|),
+ * the same spectral-radius bound as block_dt_min, without the minimum */
+static double cell_dt(const ora_grid *g, const ora_block *b, const double *u, int i, int j, int k, double cfl)
+{
+    long nfi = n_fi(b), nfj = n_fj(b), nfk = n_fk(b);
+    double Q[NV], W[NV];
+    long c0 = cell(b, i, j, k);
+    for (int q = 0; q < NV; ++q) Q[q] = u[q * b->sv + c0];
+    cons_to_prim(g->gamma, Q, W);
+    double c = sqrt(g->gamma * W[4] / W[0]);
+    double sum = 0.0;
+    for (int d = 0; d < (is2d(b) ? 2 : 3); ++d) {
+        double Sb[3];
+        for (int a = 0; a < 3; ++a) {
+            double s0, s1;
+            if (d == 0) {
+                s0 = b->Si[a * nfi + fi_index(b, i, j, k)];
+                s1 = b->Si[a * nfi + fi_index(b, i + 1, j, k)];
+            } else if (d == 1) {
+                s0 = b->Sj[a * nfj + fj_index(b, i, j, k)];
+                s1 = b->Sj[a * nfj + fj_index(b, i, j + 1, k)];
+            } else {
+                s0 = b->Sk[a * nfk + fk_index(b, i, j, k)];
+                s1 = b->Sk[a * nfk + fk_index(b, i, j, k + 1)];
+            }
+            Sb[a] = 0.5 * (s0 + s1);
+        }
+        double uS = W[1] * Sb[0] + W[2] * Sb[1] + W[3] * Sb[2];
+        double mag = sqrt(Sb[0] * Sb[0] + Sb[1] * Sb[1] + Sb[2] * Sb[2]);
+        sum += fabs(uS) + c * mag;
+    }
+    return cfl * b->vol[interior(b, i, j, k)] / sum;
+}
+
+static double rk_step_impl(const ora_grid *g, double *const *U, const double *const *src, int rk,
+                           double cfl, double dt, double *norms, int local);
+
 /* One explicit RK step (Eq. runge_kutta, Butcher form) of all blocks, in
  * place.  dt > 0 is used as given; dt <= 0 means dt = cfl * ora_dt_min(U^n).
  * norms (15 doubles, may be NULL) receives ora_norms of R(U^n) and U^n.
@@ -829,6 +866,22 @@ void ora_norms(const ora_grid *g, double *const *R, double *const *U, double *ou
  * Returns the dt used. */
 double ora_rk_step(const ora_grid *g, double *const *U, const double *const *src, int rk,
                    double cfl, double dt, double *norms)
+{
+    return rk_step_impl(g, U, src, rk, cfl, dt, norms, 0);
+}
+
+/* The same step with local time stepping (a convergence accelerator for
+ * steady states, which the paper's inlet case is): every cell advances
+ * with its own step dt_c = cfl |Omega_c| / sum_d (|u . Sbar_d| + c |Sbar_d|),
+ * evaluated on U^n and frozen over the stages.  Returns the smallest dt_c. */
+double ora_rk_step_local(const ora_grid *g, double *const *U, const double *const *src, int rk,
+                         double cfl, double *norms)
+{
+    return rk_step_impl(g, U, src, rk, cfl, 0.0, norms, 1);
+}
+
+static double rk_step_impl(const ora_grid *g, double *const *U, const double *const *src, int rk,
+                           double cfl, double dt, double *norms, int local)
 {
     double a[4][4], bw[4];
     int s = rk_tableau(rk, a, bw);
@@ -847,7 +900,26 @@ double ora_rk_step(const ora_grid *g, double *const *U, const double *const *src
         for (int i = 0; i < s; ++i) Rs[i][bi] = calloc((size_t)NV * n_interior(b), sizeof(double));
     }
     ora_fill_ghosts(g, Un);
-    if (!(dt > 0.0)) dt = cfl * ora_dt_min(g, Un);
+    double **dtc = calloc((size_t)nb, sizeof(double *));   /* per-cell steps */
+    for (int bi = 0; bi < nb; ++bi) {
+        const ora_block *b = &g->b[bi];
+        dtc[bi] = malloc(sizeof(double) * n_interior(b));
+        if (local)
+            for (int k = 0; k < b->nk; ++k)
+                for (int j = 0; j < b->nj; ++j)
+                    for (int ii = 0; ii < b->ni; ++ii)
+                        dtc[bi][interior(b, ii, j, k)] = cell_dt(g, b, Un[bi], ii, j, k, cfl);
+    }
+    if (local) {
+        dt = INFINITY;
+        for (int bi = 0; bi < nb; ++bi)
+            for (long c0 = 0; c0 < n_interior(&g->b[bi]); ++c0)
+                if (dtc[bi][c0] < dt) dt = dtc[bi][c0];
+    } else {
+        if (!(dt > 0.0)) dt = cfl * ora_dt_min(g, Un);
+        for (int bi = 0; bi < nb; ++bi)
+            for (long c0 = 0; c0 < n_interior(&g->b[bi]); ++c0) dtc[bi][c0] = dt;
+    }
 
     for (int i = 0; i < s; ++i) {
         for (int bi = 0; bi < nb; ++bi) {
@@ -861,7 +933,7 @@ double ora_rk_step(const ora_grid *g, double *const *U, const double *const *src
                         for (int q = 0; q < NV; ++q) {
                             double acc = 0.0;
                             for (int jj = 0; jj < i; ++jj) acc += a[i][jj] * Rs[jj][bi][q * nint + c0];
-                            Ui[bi][q * b->sv + cg] = Un[bi][q * b->sv + cg] - dt * acc / b->vol[c0];
+                            Ui[bi][q * b->sv + cg] = Un[bi][q * b->sv + cg] - dtc[bi][c0] * acc / b->vol[c0];
                         }
                     }
         }
@@ -880,15 +952,17 @@ double ora_rk_step(const ora_grid *g, double *const *U, const double *const *src
                     for (int q = 0; q < NV; ++q) {
                         double acc = 0.0;
                         for (int i = 0; i < s; ++i) acc += bw[i] * Rs[i][bi][q * nint + c0];
-                        U[bi][q * b->sv + cg] = Un[bi][q * b->sv + cg] - dt * acc / b->vol[c0];
+                        U[bi][q * b->sv + cg] = Un[bi][q * b->sv + cg] - dtc[bi][c0] * acc / b->vol[c0];
                     }
                 }
     }
     for (int bi = 0; bi < nb; ++bi) {
         free(Un[bi]);
         free(Ui[bi]);
+        free(dtc[bi]);
         for (int i = 0; i < s; ++i) free(Rs[i][bi]);
     }
+    free(dtc);
     for (int i = 0; i < s; ++i) free(Rs[i]);
     free(Rs);
     free(Un);

@@ -57,7 +57,7 @@ struct HostBlock {
 // sensei_workspace_size and sensei_create_grid.
 struct Plan {
     std::vector<HostBlock> blocks;
-    std::vector<size_t> off_fn, off_fn32, off_vol, off_ivol, off_ivol32, off_sbar, off_stage;
+    std::vector<size_t> off_fn, off_fn32, off_vol, off_ivol, off_ivol32, off_sbar, off_dtv, off_stage;
     size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0;
     size_t bytes = 0;
     long long max_items = 0;   // partial slots (items at the smallest k-chunk)
@@ -131,7 +131,8 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     if (st != SENSEI_OK) return st;
     size_t cur = 0;
     P.blocks.resize(nblocks);
-    for (auto *v : {&P.off_fn, &P.off_fn32, &P.off_vol, &P.off_ivol, &P.off_ivol32, &P.off_sbar, &P.off_stage})
+    for (auto *v : {&P.off_fn, &P.off_fn32, &P.off_vol, &P.off_ivol, &P.off_ivol32, &P.off_sbar, &P.off_dtv,
+                    &P.off_stage})
         v->resize(nblocks);
     const bool f32 = scheme->precision != SENSEI_FP64;
     P.two_d = blocks[0].nk == 1;
@@ -179,6 +180,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         P.off_ivol[b] = take(cur, mv * sizeof(double));
         P.off_ivol32[b] = f32 ? take(cur, mv * sizeof(float)) : 0;
         P.off_sbar[b] = take(cur, 12 * mv * sizeof(double));
+        P.off_dtv[b] = take(cur, mv * sizeof(double));
         // two FP64 stage states, or two FP32 stage states + two FP32 increments
         P.off_stage[b] = take(cur, 2 * (size_t)B.L.elems * sizeof(double));
     }
@@ -335,6 +337,7 @@ struct StencilCall {
     int mode;
     int in_slot, out_slot, dprev, dout;
     int push;
+    int local;
     double alpha, beta, gdt;
     const double *dt_slot;
     double dt_scale;
@@ -358,6 +361,7 @@ void fill_params(BatchParams<R> &p, const sensei_grid *g, const StencilCall &c)
     p.dprev = c.dprev;
     p.dout = c.dout;
     p.push = c.push;
+    p.local = c.local;
     p.gamma = (R)g->scheme.gamma;
     p.kappa = (R)g->scheme.kappa;
     p.eps = (R)g->scheme.eps;
@@ -450,9 +454,10 @@ sensei_status prepare_step(sensei_grid *g, cudaStream_t s)
     return SENSEI_OK;
 }
 
-// One RK step, launches only (capturable once prepare_step has run).
+// One RK step, launches only (capturable once prepare_step has run).  With
+// local set every cell advances by its own step cfl |Omega_c| / sum_d(...).
 sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, double cfl, double dt, double *dt_used,
-                               cudaStream_t s)
+                               cudaStream_t s, bool local = false)
 {
     sensei_status st = fill_slot(grid, SLOT_USER, U, s);
     if (st != SENSEI_OK) return st;
@@ -461,8 +466,8 @@ sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, doub
     const long long nitems = total_items(grid->plan.blocks);
     if (cfl > 0.0) {
         CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
-        CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, grid->dt_bits,
-                           grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms), s));
+        CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, local ? 1 : 0,
+                           cfl, grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms), s));
         grid->kernel_launches++;
         dt_src = (const double *)grid->dt_bits;
         dt_scale = cfl;
@@ -491,6 +496,7 @@ sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, doub
         c.partials = stage == 0;
         c.user = U;
         c.push = 1;
+        c.local = local ? 1 : 0;
         c.dprev = -1;
         c.dout = -1;
         if (!incr) {
@@ -622,6 +628,7 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
         B.ivol = (const double *)(g->ws + P.off_ivol[b]);
         B.ivol32 = P.off_ivol32[b] ? (const float *)(g->ws + P.off_ivol32[b]) : nullptr;
         B.sbar = (const double *)(g->ws + P.off_sbar[b]);
+        B.dtv = (double *)(g->ws + P.off_dtv[b]);
         B.st64[0] = (double *)(g->ws + P.off_stage[b]);
         B.st64[1] = B.st64[0] + B.L.elems;
         // FP32 storage reuses the same bytes: X0, X1, D0, D1
@@ -790,6 +797,21 @@ sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double
     cudaStream_t s = (cudaStream_t)stream;
     st = prepare_step(grid, s);
     if (st == SENSEI_OK) st = rk_step_launches(grid, U, rk, cfl, dt, dt_used, s);
+    if (st == SENSEI_OK) g_msg[0] = 0;
+    return st;
+}
+
+sensei_status sensei_rk_step_local(sensei_grid *grid, double *const *U, int rk, double cfl, double *dt_min,
+                                   sensei_stream stream)
+{
+    sensei_status st = check_step_args(grid, U, rk, cfl, 0.0);
+    if (st != SENSEI_OK) return st;
+    if (!(cfl > 0.0)) return fail(SENSEI_ERR_INVALID_ARG, "local time stepping needs cfl > 0");
+    Device dev;
+    CUDA_TRY(dev.set(grid->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    st = prepare_step(grid, s);
+    if (st == SENSEI_OK) st = rk_step_launches(grid, U, rk, cfl, 0.0, dt_min, s, true);
     if (st == SENSEI_OK) g_msg[0] = 0;
     return st;
 }

@@ -42,7 +42,8 @@ struct DtUser {
 // over the items; each thread walks its column.
 __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, int nblocks, long long nitems,
                                                       const __grid_constant__ DtUser user, double gamma,
-                                                      unsigned long long *dt_bits, unsigned *err)
+                                                      int local, double cfl, unsigned long long *dt_bits,
+                                                      unsigned *err)
 {
     const int t = threadIdx.x;
     const int ti = t % TI, tj = t / TI;
@@ -51,11 +52,11 @@ __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, in
     for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int b = find_block_item(blocks, nblocks, item);
         const BlockDev &B = blocks[b];
-        long long local = item - B.item0;
-        const int tile_i = (int)(local % B.tiles_i);
-        local /= B.tiles_i;
-        const int tile_j = (int)(local % B.tiles_j);
-        const int chunk = (int)(local / B.tiles_j);
+        long long rest = item - B.item0;
+        const int tile_i = (int)(rest % B.tiles_i);
+        rest /= B.tiles_i;
+        const int tile_j = (int)(rest % B.tiles_j);
+        const int chunk = (int)(rest / B.tiles_j);
         const int i = tile_i * TI + ti, j = tile_j * TJ + tj;
         if (i >= B.ni || j >= B.nj) continue;
         const int k0 = chunk * B.kchunk, k1 = min(k0 + B.kchunk, B.nk);
@@ -81,7 +82,9 @@ __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, in
                 double un = u * sb[m] + v * sb[mv + m] + w * sb[2 * mv + m];
                 sum += fabs(un) + a * sb[3 * mv + m];
             }
-            best = fmin(best, B.vol[m] * rcp_exact(sum));
+            const double isum = rcp_exact(sum);
+            if (local) B.dtv[m] = cfl * isum;
+            best = fmin(best, B.vol[m] * isum);
         }
     }
     if (bad) atomicOr(err, ERR_NONPHYSICAL);
@@ -125,11 +128,11 @@ __global__ void norms_finalize_kernel(const double *__restrict__ partials, int n
 }  // namespace
 
 cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
-                      unsigned long long *dt_bits, unsigned *err, int grid, cudaStream_t s)
+                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, cudaStream_t s)
 {
     DtUser u;
     for (int b = 0; b < nblocks; ++b) u.u[b] = user[b];
-    dt_kernel<<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, dt_bits, err);
+    dt_kernel<<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, local, cfl, dt_bits, err);
     return cudaGetLastError();
 }
 

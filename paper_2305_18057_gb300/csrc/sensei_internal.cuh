@@ -82,6 +82,7 @@ struct BlockDev {
     const double *vol, *ivol;
     const float *ivol32;
     const double *sbar;     // spectral metrics: 12 arrays of mvolume, index (direction*4 + q)
+    double *dtv;            // local time stepping: dt_c / |Omega| per cell (mvolume)
     double *st64[2];        // FP64 stage states
     float *xs[2], *ds[2];   // FP32 stage states and increments
     int tiles_i, tiles_j, kchunk, nchunks;
@@ -119,6 +120,7 @@ struct BatchParams {
     int in_slot, out_slot;  // out_slot: SLOT_USER / SLOT_ST* (FP64) or SLOT_X* (FP32)
     int dprev, dout;        // MODE_INCR: increment slots (0 or 1), -1 for none
     int push;
+    int local;              // local time stepping: the stage step is dtv[cell], not dt / |Omega|
     R gamma, kappa, eps, fix;
     int cons;
     double alpha, beta, gdt;
@@ -158,8 +160,10 @@ cudaError_t launch_stencil_f32s(const BatchParams<float> &p, int limiter, bool t
 int stencil_ctas_per_sm(int precision_kind, int limiter, bool two_d);
 int stencil_ctas_per_sm_f32(int precision_kind, int limiter, bool two_d);
 int stencil_ctas_per_sm_f32s(int limiter, bool two_d);
+// min over cells of |Omega| / sum_d (|u.Sbar_d| + c |Sbar_d|) into dt_bits; with local set,
+// also dtv = cfl / sum_d (...) = dt_c / |Omega| per cell
 cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
-                      unsigned long long *dt_bits, unsigned *err, int grid, cudaStream_t s);
+                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, cudaStream_t s);
 cudaError_t launch_set_scalar(double *slot, double v, cudaStream_t s);
 cudaError_t launch_scale_copy(double *dst, const double *src, double scale, cudaStream_t s);
 // Record the thread-local message returned by sensei_last_error (api.cu).

@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     const bool update = p.mode != MODE_RESIDUAL;
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
     const float gdt_dt32 = (float)(p.gdt * dt);   // MODE_INCR
+    const float gdt32 = (float)p.gdt;
     const float beta32 = (float)p.beta;
 
     // persistent: CTA x takes items x, x + grid, x + 2 grid, ...
@@ -677,7 +678,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                                       (!TWO_D && (k < 2 || k >= B.nk - 2));
                 if (p.mode == MODE_INCR && !p.partials) {
                     // FP32 increment only: no FP64 residual, no FP64 stage input
-                    const float c32 = gdt_dt32 * B.ivol32[mc];
+                    const float c32 = p.local ? gdt32 * to_f32(B.dtv[mc]) : gdt_dt32 * B.ivol32[mc];
                     if (out64) {
                         double q[NV];
 #pragma unroll
@@ -705,7 +706,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                 } else {
                     const double ivol = B.ivol[mc];
                     const double vol = B.vol[mc];
-                    const double coef = -p.gdt * dt * ivol;
+                    const double coef = p.local ? -p.gdt * B.dtv[mc] : -p.gdt * dt * ivol;
                     const long long rc = ((long long)k * B.nj + cj) * B.ni + ci;
                     const long long nint = (long long)B.ni * B.nj * B.nk;
                     double q64[NV];
@@ -722,7 +723,8 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                             q64[v] = val;
                         } else if (p.mode == MODE_INCR) {
                             // FP32 increment; FP64 accumulation on the last stage
-                            float delta = -(gdt_dt32 * B.ivol32[mc]) * (float)rres[v];
+                            const float c32 = p.local ? gdt32 * to_f32(B.dtv[mc]) : gdt_dt32 * B.ivol32[mc];
+                            float delta = -c32 * (float)rres[v];
                             if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
                             if (out64) {
                                 q64[v] = un[cell + v * L.sv] + to_f64(delta);

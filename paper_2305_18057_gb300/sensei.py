@@ -29,7 +29,7 @@ NV = 5
 # every symbol include/sensei.h declares
 EXPORTS = ("sensei_workspace_size", "sensei_create_grid", "sensei_destroy_grid", "sensei_state_layout",
            "sensei_set_bc", "sensei_fill_ghosts", "sensei_residual", "sensei_rk_step", "sensei_norms",
-           "sensei_step_graph_create", "sensei_step_graph_launch", "sensei_step_graph_destroy", "sensei_autotune",
+           "sensei_rk_step_local", "sensei_step_graph_create", "sensei_step_graph_launch", "sensei_step_graph_destroy", "sensei_autotune",
            "sensei_profile_enable", "sensei_profile_read", "sensei_residual_norms_noalloc", "sensei_last_error")
 
 
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
     L.sensei_residual.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]
     L.sensei_rk_step.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_double, C.c_double, vp, vp]
     L.sensei_norms.argtypes = [vp, dp, dp, dp, vp]
+    L.sensei_rk_step_local.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_double, vp, vp]
     L.sensei_step_graph_create.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_double, C.c_double, vp, vp,
                                            C.POINTER(vp)]
     L.sensei_step_graph_launch.argtypes = [vp, vp]
@@ -157,6 +158,10 @@ def sensei_norms(grid, stream_ptr, check=True):
     if check:
         _check(st)
     return st, np.array(l2[:]), np.array(linf[:]), np.array(cons[:])
+
+
+def sensei_rk_step_local(grid, U_ptrs, rk, cfl, dt_min_ptr, stream_ptr):
+    return _check(load().sensei_rk_step_local(grid, _ptrs(U_ptrs), rk, cfl, dt_min_ptr, stream_ptr))
 
 
 def sensei_step_graph_create(grid, U_ptrs, rk, cfl, dt, dt_used_ptr, stream_ptr):
@@ -297,6 +302,10 @@ class Grid:
 
     def norms(self, check=True):
         return sensei_norms(self.handle, self.sptr, check=check)
+
+    def rk_step_local(self, Us, rk=RK3_SSP, cfl=0.5, dt_min=None):
+        sensei_rk_step_local(self.handle, [U.data_ptr() for U in Us], rk, cfl,
+                             dt_min.data_ptr() if dt_min is not None else None, self.sptr)
 
     def step_graph(self, Us, rk=RK3_SSP, cfl=0.5, dt=0.0, dt_used=None):
         """A replayable CUDA graph of one rk_step on these states."""

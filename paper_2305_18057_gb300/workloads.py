@@ -167,14 +167,16 @@ def geometric_spacing(n, ratio):
     return np.expm1(j * math.log(ratio)) / math.expm1(n * math.log(ratio))
 
 
-def ramp_nodes(ni, nj, nk, length=2.0, height=1.0, corner=0.5, angle_deg=10.0, ratio=1.02, depth=1.0):
+def ramp_nodes(ni, nj, nk, length=2.0, height=1.0, corner=0.5, angle_deg=10.0, ratio=1.02, depth=1.0, stride=1):
     """Compression ramp: wall y_w(x) = max(0, x - corner) tan(angle), top wall
     at y = height, j-nodes geometric with `ratio` away from the ramp; k is an
-    extrusion over `depth` (a single unit-depth cell layer in 2D)."""
-    x = length * np.arange(ni + 1) / ni
+    extrusion over `depth` (a single unit-depth cell layer in 2D).  With
+    stride > 1 the grid is every stride-th node of the (stride*ni) x
+    (stride*nj) x (stride*nk) grid (a node restriction)."""
+    x = length * np.arange(stride * ni + 1)[::stride] / (stride * ni)
     yw = np.maximum(0.0, x - corner) * math.tan(math.radians(angle_deg))
-    s = geometric_spacing(nj, ratio)
-    zs = (depth if nk > 1 else 1.0) * np.arange(nk + 1) / nk
+    s = geometric_spacing(stride * nj, ratio)[::stride]
+    zs = (depth if nk > 1 else 1.0) * np.arange(stride * nk + 1)[::stride] / (stride * nk)
     X = np.empty((3, nk + 1, nj + 1, ni + 1))
     X[0] = x[None, None, :]
     X[1] = yw[None, None, :] + (height - yw[None, None, :]) * s[None, :, None]
@@ -251,13 +253,16 @@ def periodic_3d(n=256, seed=2307, mach=2.5, limiter="vanleer", steps=100, nj=Non
                     rk="rk3", cfl=0.5, steps=steps)
 
 
-def ramp_3d(n=512, ratio=1.005, angle_deg=8.0, steps=50, ni=None, nj=None, nk=None, perturb=0.0, seed=2310):
+def ramp_3d(n=512, ratio=1.005, angle_deg=8.0, steps=50, ni=None, nj=None, nk=None, perturb=0.0, seed=2310,
+            restrict=1):
     """3D Mach-4 compression ramp, 8-deg ramp extruded in k (periodic in k),
-    wall-normal geometric stretching `ratio`, the paper's inflow state."""
+    wall-normal geometric stretching `ratio`, the paper's inflow state.
+    restrict = r > 1: the grid of every r-th node of the r-times finer grid
+    (e.g. n = 128, restrict = 4: the 128^3 restriction of the 512^3 grid)."""
     ni = n if ni is None else ni
     nj = n if nj is None else nj
     nk = n if nk is None else nk
-    X = ramp_nodes(ni, nj, nk, ratio=ratio, angle_deg=angle_deg, depth=1.0)
+    X = ramp_nodes(ni, nj, nk, ratio=ratio, angle_deg=angle_deg, depth=1.0, stride=restrict)
     prim = inlet_inflow()
     U0 = uniform_state((ni, nj, nk), prim, perturb=perturb, seed=seed)
     bcs = [BC(INFLOW, prim), BC(EXTRAPOLATE), BC(SLIP_WALL), BC(INFLOW, prim), BC(PERIODIC), BC(PERIODIC)]

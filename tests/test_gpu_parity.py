@@ -180,3 +180,36 @@ def test_autotuned_schedule_keeps_parity(case):
     torch.cuda.synchronize()
     for b in range(len(w.dims)):
         assert per_var_rel(g.download(Us[b], b), og.interior(Uo[b], b)) < 1e-9, b
+
+
+@pytest.mark.parametrize("case", ["periodic3d_odd", "ramp2d", "lattice"])
+def test_local_time_stepping_parity(case):
+    w = CASES[case]()
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    g = gpu_grid(w)
+    Us = gpu_states(g, w)
+    dt_min = torch.zeros(1, dtype=torch.float64, device=Us[0].device)
+    for _ in range(20):
+        g.rk_step_local(Us, RK["rk3"], cfl=0.6, dt_min=dt_min)
+        dto, _ = og.rk_step_local(Uo, RK["rk3"], cfl=0.6)
+        assert abs(dt_min.item() - dto) <= 1e-11 * dto
+    torch.cuda.synchronize()
+    for b in range(len(w.dims)):
+        assert per_var_rel(g.download(Us[b], b), og.interior(Uo[b], b)) < 1e-9, (case, b)
+
+
+def test_local_time_stepping_converges_on_gpu():
+    # the stretched Mach-4 ramp of the oracle's pin, marched to round-off
+    from test_oracle_lts import _ramp
+    w = _ramp()
+    for prec in (0, 2):
+        g = gpu_grid(w, precision=prec)
+        Us = gpu_states(g, w)
+        g.rk_step_local(Us, RK["rk3"], cfl=0.8)
+        l2_0 = g.norms()[1][0]
+        for _ in range(1500):
+            g.rk_step_local(Us, RK["rk3"], cfl=0.8)
+        l2 = g.norms()[1][0]
+        # FP64 reaches round-off; FP32 storage stalls at its own rounding level
+        assert l2 < (1e-9 if prec == 0 else 1e-4) * l2_0, (prec, l2 / l2_0)
