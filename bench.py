@@ -315,6 +315,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-perf-model", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="grid size override (c3, c5): small profiling cases")
     ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the step (default for c4)")
     args = ap.parse_args()
@@ -483,6 +484,25 @@ def main():
                              "kernel_ms_per_launch": stv, "alg_bytes_per_launch": bv, "peak_source": peak_src}}
             del gv, Uv
         del g64, U64
+
+    # the performance model of Sec. 6 on this GPU: the 2D ramp at three N_l
+    # with N_w = 1024, each cut into P = 1, 4, 16, 64 i-blocks (the model's
+    # 1D decomposition along N_l); fitted t_I, t_B, beta of the FP64 step
+    if world == 1 and not args.no_perf_model:
+        from paper_2305_18057_gb300 import perfmodel, workloads as wl
+        sizes = (2048, 4096, 8192)
+        rows, fit = perfmodel.decomposition_study(
+            [wl.ramp_2d(ni=n, nj=1024) for n in sizes], (1, 4, 16, 64),
+            lambda w_: gpu_setup(w_, sensei.FP64)[:2], steps=10, warmup=3)
+        line["perf_model"] = {
+            "workload": "ramp2d N_l x 1024, N_l in {2048, 4096, 8192}, cut into P in {1, 4, 16, 64} i-blocks, "
+                        "FP64 SSPRK3 step",
+            "fit": "T_step = N t_I + N_B t_B + t_0 (N_B = cells on block faces)",
+            "t_I_ns": fit["t_I"] * 1e9, "t_B_ns": fit["t_B"] * 1e9, "t_0_us": fit["t_0"] * 1e6,
+            "beta": fit["beta"], "max_rel_dev": fit["max_rel_dev"],
+            "samples": [[r["dims"][0], r["parts"], r["boundary_cells"], round(r["step_s"] * 1e3, 4)]
+                        for r in rows],
+            "samples_cols": ["N_l", "P", "N_B", "ms_per_step"]}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs, sample, _ = oracle_sample(args.workload, 3 if args.workload in ("c3", "c5") else 2, 0)

@@ -319,3 +319,33 @@ def restrict_nodes(X, stride):
     """Every `stride`-th node of a grid (the coarse grid of a node restriction)."""
     return np.ascontiguousarray(X[:, ::stride, ::stride, ::stride]) if X.shape[1] > 2 else \
         np.ascontiguousarray(X[:, :, ::stride, ::stride])
+
+
+def split_i(w, parts):
+    """The same grid, state and boundary conditions cut into `parts` blocks
+    along i (the 1D decomposition along N_l of the performance model, Sec. 6):
+    block p holds i-cells [o_p, o_{p+1}) with o_p = floor(p ni / parts); cut
+    faces become block interfaces, an i-periodic pair becomes the interface
+    between the last and the first block.  Single-block workloads only."""
+    assert len(w.dims) == 1 and 1 <= parts <= w.dims[0][0]
+    ni, nj, nk = w.dims[0]
+    X, U0, faces = w.nodes[0], w.U0[0], w.bcs[0]
+    o = [(p * ni) // parts for p in range(parts + 1)]
+    dims, nodes, states, bcs = [], [], [], []
+    periodic_i = faces[IMIN].type == PERIODIC
+    for p in range(parts):
+        dims.append((o[p + 1] - o[p], nj, nk))
+        nodes.append(np.ascontiguousarray(X[:, :, :, o[p]:o[p + 1] + 1]))
+        states.append(np.ascontiguousarray(U0[:, :, :, o[p]:o[p + 1]]))
+        f = list(faces)
+        if p > 0:
+            f[IMIN] = BC(INTERFACE, None, p - 1, IMAX)
+        elif periodic_i and parts > 1:
+            f[IMIN] = BC(INTERFACE, None, parts - 1, IMAX)
+        if p < parts - 1:
+            f[IMAX] = BC(INTERFACE, None, p + 1, IMIN)
+        elif periodic_i and parts > 1:
+            f[IMAX] = BC(INTERFACE, None, 0, IMIN)
+        bcs.append(f)
+    return dataclasses.replace(w, name=f"{w.name}/split{parts}", dims=dims, nodes=nodes, U0=states, bcs=bcs,
+                               note=(w.note + f" cut into {parts} i-blocks").strip())
