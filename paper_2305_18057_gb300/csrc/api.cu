@@ -57,7 +57,7 @@ struct HostBlock {
 // sensei_workspace_size and sensei_create_grid.
 struct Plan {
     std::vector<HostBlock> blocks;
-    std::vector<size_t> off_fn, off_fn32, off_vol, off_ivol, off_ivol32, off_sbar, off_dtv, off_stage;
+    std::vector<size_t> off_fn, off_rec32, off_vol, off_ivol, off_sbar, off_dtv, off_stage;
     size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0;
     size_t bytes = 0;
     long long max_items = 0;   // partial slots (items at the smallest k-chunk)
@@ -131,7 +131,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     if (st != SENSEI_OK) return st;
     size_t cur = 0;
     P.blocks.resize(nblocks);
-    for (auto *v : {&P.off_fn, &P.off_fn32, &P.off_vol, &P.off_ivol, &P.off_ivol32, &P.off_sbar, &P.off_dtv,
+    for (auto *v : {&P.off_fn, &P.off_rec32, &P.off_vol, &P.off_ivol, &P.off_sbar, &P.off_dtv,
                     &P.off_stage})
         v->resize(nblocks);
     const bool f32 = scheme->precision != SENSEI_FP64;
@@ -175,10 +175,10 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         P.ncells += (long long)d.ni * d.nj * d.nk;
         const size_t mv = (size_t)B.ml.mvolume;
         P.off_fn[b] = take(cur, 12 * mv * sizeof(double));
-        P.off_fn32[b] = f32 ? take(cur, 12 * mv * sizeof(float)) : 0;
+        P.off_rec32[b] =
+            f32 ? take(cur, (size_t)B.tiles_i * B.tiles_j * d.nk * REC * sizeof(float)) : 0;
         P.off_vol[b] = take(cur, mv * sizeof(double));
         P.off_ivol[b] = take(cur, mv * sizeof(double));
-        P.off_ivol32[b] = f32 ? take(cur, mv * sizeof(float)) : 0;
         P.off_sbar[b] = take(cur, 12 * mv * sizeof(double));
         P.off_dtv[b] = take(cur, mv * sizeof(double));
         // two FP64 stage states, or two FP32 stage states + two FP32 increments
@@ -623,10 +623,9 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
         BlockDev &B = g->plan.blocks[b].dev;
         const size_t mv = (size_t)B.ml.mvolume;
         B.fn = (const double *)(g->ws + P.off_fn[b]);
-        B.fn32 = P.off_fn32[b] ? (const float *)(g->ws + P.off_fn32[b]) : nullptr;
+        B.rec32 = P.off_rec32[b] ? (const float *)(g->ws + P.off_rec32[b]) : nullptr;
         B.vol = (const double *)(g->ws + P.off_vol[b]);
         B.ivol = (const double *)(g->ws + P.off_ivol[b]);
-        B.ivol32 = P.off_ivol32[b] ? (const float *)(g->ws + P.off_ivol32[b]) : nullptr;
         B.sbar = (const double *)(g->ws + P.off_sbar[b]);
         B.dtv = (double *)(g->ws + P.off_dtv[b]);
         B.st64[0] = (double *)(g->ws + P.off_stage[b]);
@@ -641,13 +640,12 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
         for (int fam = 0; fam < 3; ++fam)
             for (int q = 0; q < 4; ++q) {
                 mo.n[fam][q] = (double *)B.fn + (fam * 4 + q) * mv;
-                mo.n32[fam][q] = B.fn32 ? (float *)B.fn32 + (fam * 4 + q) * mv : nullptr;
                 mo.sbar[fam][q] = (double *)B.sbar + (fam * 4 + q) * mv;
             }
         mo.vol = (double *)B.vol;
         mo.ivol = (double *)B.ivol;
-        mo.ivol32 = (float *)B.ivol32;
         cudaError_t e = launch_metrics(B.ni, B.nj, B.nk, nodes[b], mo, B.ml, s);
+        if (e == cudaSuccess) e = launch_pack_records(B, s);
         if (e != cudaSuccess) {
             delete g;
             return fail(SENSEI_ERR_CUDA, "metrics kernel: %s", cudaGetErrorString(e));

@@ -83,10 +83,7 @@ __global__ void metrics_kernel(int ni, int nj, int nk, const double *__restrict_
             double a = sqrt(s.x * s.x + s.y * s.y + s.z * s.z);
             double inv = a > 0.0 ? 1.0 / a : 0.0;
             double v[4] = {s.x * inv, s.y * inv, s.z * inv, a};
-            for (int q = 0; q < 4; ++q) {
-                mo.n[fam][q][m] = v[q];
-                if (mo.n32[fam][q]) mo.n32[fam][q][m] = (float)v[q];
-            }
+            for (int q = 0; q < 4; ++q) mo.n[fam][q][m] = v[q];
         }
         if (in_i && in_j && in_k) {
             // |Omega| = (1/3) sum over the six faces of centroid . outward area
@@ -110,8 +107,46 @@ __global__ void metrics_kernel(int ni, int nj, int nk, const double *__restrict_
             vol = vol / 3.0;
             mo.vol[m] = vol;
             mo.ivol[m] = 1.0 / vol;
-            if (mo.ivol32) mo.ivol32[m] = (float)(1.0 / vol);
         }
+    }
+}
+
+// The FP32 records of the FP32 stencil: record (tile_i, tile_j, k) holds
+// the tile's i-faces, j-faces and upper k-faces (unit normal, area) and
+// 1/|Omega| of its cells, rounded to FP32; entries outside the block are 0.
+__global__ void pack_records_kernel(BlockDev B)
+{
+    const long long nrec = (long long)B.tiles_i * B.tiles_j * B.nk;
+    const long long mv = B.ml.mvolume;
+    float *rec = const_cast<float *>(B.rec32);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nrec * REC;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / REC;
+        int e = (int)(t - r * REC);
+        const int tile_i = (int)(r % B.tiles_i);
+        const int tile_j = (int)((r / B.tiles_i) % B.tiles_j);
+        const int k = (int)(r / ((long long)B.tiles_i * B.tiles_j));
+        const int i0 = tile_i * TI, j0 = tile_j * TJ;
+        double v = 0.0;
+        if (e < REC_I) {
+            const int q = e / (TJ * (TI + 1)), rem = e % (TJ * (TI + 1));
+            const int i = i0 + rem % (TI + 1), j = j0 + rem / (TI + 1);
+            if (i <= B.ni && j < B.nj) v = B.fn[q * mv + k * B.ml.mplane + j * B.ml.mpitch + i];
+        } else if ((e -= REC_I) < REC_J) {
+            const int q = e / ((TJ + 1) * TI), rem = e % ((TJ + 1) * TI);
+            const int i = i0 + rem % TI, j = j0 + rem / TI;
+            if (i < B.ni && j <= B.nj) v = B.fn[(4 + q) * mv + k * B.ml.mplane + j * B.ml.mpitch + i];
+        } else if ((e -= REC_J) < REC_K) {
+            const int q = e / (TJ * TI), rem = e % (TJ * TI);
+            const int i = i0 + rem % TI, j = j0 + rem / TI;
+            if (i < B.ni && j < B.nj && B.nk > 1)
+                v = B.fn[(8 + q) * mv + (k + 1) * B.ml.mplane + j * B.ml.mpitch + i];
+        } else {
+            e -= REC_K;
+            const int i = i0 + e % TI, j = j0 + e / TI;
+            if (i < B.ni && j < B.nj) v = B.ivol[k * B.ml.mplane + j * B.ml.mpitch + i];
+        }
+        rec[t] = (float)v;
     }
 }
 
@@ -205,6 +240,16 @@ cudaError_t launch_metrics(int ni, int nj, int nk, const double *X, const Metric
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     metrics_kernel<<<(unsigned)blocks, 256, 0, s>>>(ni, nj, nk, X, mo, ml);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_records(const BlockDev &B, cudaStream_t s)
+{
+    if (!B.rec32) return cudaSuccess;
+    const long long total = (long long)B.tiles_i * B.tiles_j * B.nk * REC;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    pack_records_kernel<<<(unsigned)blocks, 256, 0, s>>>(B);
     return cudaGetLastError();
 }
 

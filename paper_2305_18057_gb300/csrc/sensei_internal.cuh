@@ -19,6 +19,19 @@ constexpr int NTHREADS = TI * TJ;
 
 // Error bits OR-ed into the device error word.
 constexpr unsigned ERR_NONPHYSICAL = 1u;
+constexpr unsigned ERR_TIMEOUT = 2u;     // a bounded wait on an asynchronous copy gave up
+
+// The FP32 stencil's face-metric record of one (tile, k-plane): the unit
+// normal and area (4 components, component-major) of the tile's i-faces
+// (TJ rows x TI+1), j-faces (TJ+1 rows x TI) and upper k-faces (TJ x TI),
+// then 1/|Omega| of its cells (TJ x TI); entries outside the block are 0.
+// Records are stored k-plane-major: ((k * tiles_j + tile_j) * tiles_i + tile_i).
+constexpr int REC_I = 4 * TJ * (TI + 1);
+constexpr int REC_J = 4 * (TJ + 1) * TI;
+constexpr int REC_K = 4 * TJ * TI;
+constexpr int REC_V = TJ * TI;
+constexpr int REC = REC_I + REC_J + REC_K + REC_V;
+static_assert((REC * 4) % 16 == 0, "a record is one 16-byte-multiple bulk copy");
 
 // ------------------------------------------------------------------------
 // One block's state array: element  base[off + v*sv + k*sk + j*sj + i].
@@ -37,18 +50,6 @@ struct StateLayout {
 // and the area |S| of the face with lowest corner node (i, j, k).  Cell
 // arrays use the entries with i < ni, j < nj, k < nk.
 // ------------------------------------------------------------------------
-template <typename R>
-struct FaceMetrics {
-    const R *n[3][4];       // [family][nx, ny, nz, area]
-};
-
-struct CellMetrics {
-    const double *vol;      // |Omega|
-    const double *ivol;     // 1 / |Omega|
-    const float *ivol32;    // 1 / |Omega| rounded to FP32 (FP32-storage stages)
-    const double *sbar[3][4];   // per direction d: mean area vector of the two d-faces (3), its length
-};
-
 struct MetricLayout {
     long long mpitch, mplane, mvolume;
 };
@@ -56,9 +57,7 @@ struct MetricLayout {
 // Mutable pointers for the metrics kernel.
 struct MetricsOut {
     double *n[3][4];
-    float *n32[3][4];       // FP32 copies for the FP32-flux stencil (may be null)
     double *vol, *ivol;
-    float *ivol32;          // may be null
     double *sbar[3][4];
 };
 
@@ -78,9 +77,8 @@ struct BlockDev {
     StateLayout L;
     MetricLayout ml;
     const double *fn;       // face metrics: 12 arrays of mvolume, index (family*4 + q)
-    const float *fn32;      // their FP32 copies (null in FP64 mode)
+    const float *rec32;     // FP32 face-metric records of the FP32 stencil (null in FP64 mode)
     const double *vol, *ivol;
-    const float *ivol32;
     const double *sbar;     // spectral metrics: 12 arrays of mvolume, index (direction*4 + q)
     double *dtv;            // local time stepping: dt_c / |Omega| per cell (mvolume)
     double *st64[2];        // FP64 stage states
@@ -149,6 +147,8 @@ struct BCBatch {
 cudaError_t launch_metrics(int ni, int nj, int nk, const double *X, const MetricsOut &mo,
                            const MetricLayout &ml, cudaStream_t s);
 cudaError_t launch_bc(const BCBatch &p, cudaStream_t s);
+// pack block B's FP64 face metrics and 1/|Omega| into its FP32 records B.rec32
+cudaError_t launch_pack_records(const BlockDev &B, cudaStream_t s);
 // FP64 arithmetic on an FP64 state
 cudaError_t launch_stencil_f64(const BatchParams<double> &p, int limiter, bool two_d, int grid, cudaStream_t s);
 // FP32 arithmetic on an FP64 state (FP32 flux; first FP32-storage stage; residuals)

@@ -59,7 +59,7 @@ struct SmemLayout {
 // dissipation or a limited slope), STEPS = 2 reaches the correctly rounded
 // value (used where it enters the state or the central flux).  The
 // reciprocal step is r' = r + r (1 - d r); the rsqrt step
-// y' = y + (y/2) (1 - x y^2).  FP32: the single-precision intrinsics.
+// y' = y + (y/2) (1 - x y^2).  FP32: the approximations alone (below).
 template <int STEPS>
 __device__ __forceinline__ double rcp_nr(double d)
 {
@@ -92,17 +92,30 @@ template <>
 __device__ __forceinline__ double rcp_t<double, 1>(double x) { return rcp_nr<1>(x); }
 template <>
 __device__ __forceinline__ double rcp_t<double, 2>(double x) { return rcp_nr<2>(x); }
+// FP32: the single-precision approximations (about 1 ulp), flush-to-zero
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 template <>
-__device__ __forceinline__ float rcp_t<float, 1>(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp_t<float, 1>(float x) { return rcp_approx(x); }
 template <>
-__device__ __forceinline__ float rcp_t<float, 2>(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp_t<float, 2>(float x) { return rcp_approx(x); }
 
 template <typename R>
 __device__ __forceinline__ R rsqrt1_t(R x);
 template <>
 __device__ __forceinline__ double rsqrt1_t<double>(double x) { return rsqrt_nr<1>(x); }
 template <>
-__device__ __forceinline__ float rsqrt1_t<float>(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float rsqrt1_t<float>(float x) { return rsqrt_approx(x); }
 
 // x > 0 (nonzero, not NaN) and the sign of x, from the bit pattern (integer
 // pipe, keeps compares off the FP64 pipe)
@@ -337,8 +350,6 @@ template <typename R>
 __device__ __forceinline__ const R *face_metric_base(const BlockDev &B);
 template <>
 __device__ __forceinline__ const double *face_metric_base<double>(const BlockDev &B) { return B.fn; }
-template <>
-__device__ __forceinline__ const float *face_metric_base<float>(const BlockDev &B) { return B.fn32; }
 
 // The output buffer of a stage for block n: FP64 (the caller's U or an FP64
 // stage state) or FP32 (an FP32 stage state).
@@ -449,9 +460,6 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     const int cons = p.cons;
     const bool update = p.mode != MODE_RESIDUAL;
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
-    const float gdt_dt32 = (float)(p.gdt * dt);   // MODE_INCR
-    const float gdt32 = (float)p.gdt;
-    const float beta32 = (float)p.beta;
 
     // persistent: CTA x takes items x, x + grid, x + 2 grid, ...
     for (long long item = blockIdx.x; item < p.nitems; item += gridDim.x) {
@@ -481,10 +489,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                            ? reinterpret_cast<const TS *>(slot32(B, p.in_slot))
                            : reinterpret_cast<const TS *>(slot64(B, p.user[b], p.in_slot));
         const double *un = p.user[b];
-        double *out64 = (p.mode != MODE_RESIDUAL && p.out_slot < SLOT_X0) ? slot64(B, p.user[b], p.out_slot) : nullptr;
-        float *xout = (p.mode == MODE_INCR && p.out_slot >= SLOT_X0) ? slot32(B, p.out_slot) : nullptr;
-        const float *dprev = p.dprev >= 0 ? B.ds[p.dprev] : nullptr;
-        float *dout = p.dout >= 0 ? B.ds[p.dout] : nullptr;
+        double *out64 = p.mode == MODE_ACCUM ? slot64(B, p.user[b], p.out_slot) : nullptr;
         CellLoader<R, TS> ld{in, L, B.ni, B.nj, B.nk};
 
         // per-thread FP64 norm accumulators (touched once per plane; under
@@ -676,41 +681,13 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                 }
                 const bool boundary = ci < 2 || ci >= B.ni - 2 || cj < 2 || cj >= B.nj - 2 ||
                                       (!TWO_D && (k < 2 || k >= B.nk - 2));
-                if (p.mode == MODE_INCR && !p.partials) {
-                    // FP32 increment only: no FP64 residual, no FP64 stage input
-                    const float c32 = p.local ? gdt32 * to_f32(B.dtv[mc]) : gdt_dt32 * B.ivol32[mc];
-                    if (out64) {
-                        double q[NV];
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) {
-                            float delta = -c32 * (float)rres[v];
-                            if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
-                            q[v] = un[cell + v * L.sv] + to_f64(delta);
-                            out64[cell + v * L.sv] = q[v];
-                        }
-                        if (p.push && boundary) push_ghosts<double>(p, B, b, ci, cj, k, q, NFACES);
-                    } else {
-                        float q[NV];
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) {
-                            float delta = -c32 * (float)rres[v];
-                            if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
-                            const float xc = sizeof(TS) == 8 ? cvt<float, TS>(in[cell + v * L.sv])
-                                                             : to_f32(un[cell + v * L.sv]);
-                            dout[cell + v * L.sv] = delta;
-                            q[v] = xc + delta;
-                            xout[cell + v * L.sv] = q[v];
-                        }
-                        if (p.push && boundary) push_ghosts<float>(p, B, b, ci, cj, k, q, NFACES);
-                    }
-                } else {
+                {
                     const double ivol = B.ivol[mc];
                     const double vol = B.vol[mc];
                     const double coef = p.local ? -p.gdt * B.dtv[mc] : -p.gdt * dt * ivol;
                     const long long rc = ((long long)k * B.nj + cj) * B.ni + ci;
                     const long long nint = (long long)B.ni * B.nj * B.nk;
                     double q64[NV];
-                    float q32[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         double r = cvt<double, R>(rres[v]);
@@ -721,24 +698,6 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                             if (p.alpha != 0.0) val += p.alpha * un[cell + v * L.sv];
                             out64[cell + v * L.sv] = val;
                             q64[v] = val;
-                        } else if (p.mode == MODE_INCR) {
-                            // FP32 increment; FP64 accumulation on the last stage
-                            const float c32 = p.local ? gdt32 * to_f32(B.dtv[mc]) : gdt_dt32 * B.ivol32[mc];
-                            float delta = -c32 * (float)rres[v];
-                            if (dprev) delta = fmaf(beta32, dprev[cell + v * L.sv], delta);
-                            if (out64) {
-                                q64[v] = un[cell + v * L.sv] + to_f64(delta);
-                                out64[cell + v * L.sv] = q64[v];
-                            } else {
-                                // the FP32 image of U^n: the loaded input on
-                                // the first stage, else rounded from the
-                                // FP64 master
-                                const float xc = sizeof(TS) == 8 ? cvt<float, TS>(in[cell + v * L.sv])
-                                                                 : to_f32(un[cell + v * L.sv]);
-                                dout[cell + v * L.sv] = delta;
-                                q32[v] = xc + delta;
-                                xout[cell + v * L.sv] = q32[v];
-                            }
                         } else {
                             p.rout[b][v * nint + rc] = r;
                         }
@@ -748,12 +707,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                             ncons[v] = fma(vol, uin, ncons[v]);
                         }
                     }
-                    if (p.push && boundary && p.mode != MODE_RESIDUAL) {
-                        if (out64)
-                            push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
-                        else
-                            push_ghosts<float>(p, B, b, ci, cj, k, q32, NFACES);
-                    }
+                    if (p.push && boundary && p.mode == MODE_ACCUM) push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
                 }
             }
             if (!TWO_D) {

@@ -1,13 +1,12 @@
-// stencil_f32s.cu -- FP32-arithmetic instantiations of the fused stencil
-// kernel on an FP32 stage state (the stages after the first of the
-// FP32-storage mode).
-#include "stencil.cuh"
+// stencil_f32s.cu -- the FP32-arithmetic stencil kernel on an FP32 stage
+// state (the stages after the first of the FP32-storage mode).
+#include "stencil32.cuh"
 
 namespace sensei {
 cudaError_t launch_stencil_f32s(const BatchParams<float> &p, int limiter, bool two_d, int grid, cudaStream_t s)
 {
-    return StencilLauncher<float, float>::launch(p, limiter, two_d, grid, s);
+    return Stencil32Launcher<float>::launch(p, limiter, two_d, grid, s);
 }
 
-int stencil_ctas_per_sm_f32s(int limiter, bool two_d) { return StencilLauncher<float, float>::ctas_per_sm(limiter, two_d); }
+int stencil_ctas_per_sm_f32s(int limiter, bool two_d) { return Stencil32Launcher<float>::ctas_per_sm(limiter, two_d); }
 }  // namespace sensei
