@@ -57,7 +57,7 @@ struct HostBlock {
 // sensei_workspace_size and sensei_create_grid.
 struct Plan {
     std::vector<HostBlock> blocks;
-    std::vector<size_t> off_fn, off_rec32, off_vol, off_ivol, off_sbar, off_dtv, off_stage;
+    std::vector<size_t> off_fn, off_rec32, off_vol, off_ivol, off_sbar, off_sbar32, off_dtv, off_stage;
     size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0;
     size_t bytes = 0;
     long long max_items = 0;   // partial slots (items at the smallest k-chunk)
@@ -131,7 +131,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     if (st != SENSEI_OK) return st;
     size_t cur = 0;
     P.blocks.resize(nblocks);
-    for (auto *v : {&P.off_fn, &P.off_rec32, &P.off_vol, &P.off_ivol, &P.off_sbar, &P.off_dtv,
+    for (auto *v : {&P.off_fn, &P.off_rec32, &P.off_vol, &P.off_ivol, &P.off_sbar, &P.off_sbar32, &P.off_dtv,
                     &P.off_stage})
         v->resize(nblocks);
     const bool f32 = scheme->precision != SENSEI_FP64;
@@ -180,6 +180,8 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         P.off_vol[b] = take(cur, mv * sizeof(double));
         P.off_ivol[b] = take(cur, mv * sizeof(double));
         P.off_sbar[b] = take(cur, 12 * mv * sizeof(double));
+        // FP32 spectral metrics (12 arrays) and |Omega| (1) for the FP32 time step
+        P.off_sbar32[b] = f32 ? take(cur, 13 * mv * sizeof(float)) : 0;
         P.off_dtv[b] = take(cur, mv * sizeof(double));
         // two FP64 stage states, or two FP32 stage states + two FP32 increments
         P.off_stage[b] = take(cur, 2 * (size_t)B.L.elems * sizeof(double));
@@ -467,7 +469,8 @@ sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, doub
     if (cfl > 0.0) {
         CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
         CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, local ? 1 : 0,
-                           cfl, grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms), s));
+                           cfl, grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms),
+                           grid->scheme.precision != SENSEI_FP64, s));
         grid->kernel_launches++;
         dt_src = (const double *)grid->dt_bits;
         dt_scale = cfl;
@@ -627,6 +630,8 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
         B.vol = (const double *)(g->ws + P.off_vol[b]);
         B.ivol = (const double *)(g->ws + P.off_ivol[b]);
         B.sbar = (const double *)(g->ws + P.off_sbar[b]);
+        B.sbar32 = P.off_sbar32[b] ? (const float *)(g->ws + P.off_sbar32[b]) : nullptr;
+        B.vol32 = B.sbar32 ? B.sbar32 + 12 * mv : nullptr;
         B.dtv = (double *)(g->ws + P.off_dtv[b]);
         B.st64[0] = (double *)(g->ws + P.off_stage[b]);
         B.st64[1] = B.st64[0] + B.L.elems;
@@ -641,9 +646,11 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
             for (int q = 0; q < 4; ++q) {
                 mo.n[fam][q] = (double *)B.fn + (fam * 4 + q) * mv;
                 mo.sbar[fam][q] = (double *)B.sbar + (fam * 4 + q) * mv;
+                mo.sbar32[fam][q] = B.sbar32 ? (float *)B.sbar32 + (fam * 4 + q) * mv : nullptr;
             }
         mo.vol = (double *)B.vol;
         mo.ivol = (double *)B.ivol;
+        mo.vol32 = (float *)B.vol32;
         cudaError_t e = launch_metrics(B.ni, B.nj, B.nk, nodes[b], mo, B.ml, s);
         if (e == cudaSuccess) e = launch_pack_records(B, s);
         if (e != cudaSuccess) {

@@ -103,10 +103,13 @@ __global__ void metrics_kernel(int ni, int nj, int nk, const double *__restrict_
                 mo.sbar[fam][1][m] = sb.y;
                 mo.sbar[fam][2][m] = sb.z;
                 mo.sbar[fam][3][m] = sqrt(sb.x * sb.x + sb.y * sb.y + sb.z * sb.z);
+                if (mo.vol32)
+                    for (int q = 0; q < 4; ++q) mo.sbar32[fam][q][m] = (float)mo.sbar[fam][q][m];
             }
             vol = vol / 3.0;
             mo.vol[m] = vol;
             mo.ivol[m] = 1.0 / vol;
+            if (mo.vol32) mo.vol32[m] = (float)vol;
         }
     }
 }

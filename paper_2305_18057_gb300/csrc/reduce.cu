@@ -2,7 +2,8 @@
 //
 // dt = cfl * min over cells of |Omega| / sum_d (|u . Sbar_d| + c |Sbar_d|)
 // (the paper states no time-step rule; this spectral-radius bound is the
-// reading used).  The minimum of positive doubles is taken with an integer
+// reading used), in FP64, or for the mixed-precision modes in FP32 (a time
+// step within a few FP32 ulps of the FP64 one: any such dt is as stable).  The minimum of positive doubles is taken with an integer
 // atomicMin on their bit patterns, which order like the values, so the
 // result is exact and independent of the order.
 //
@@ -38,16 +39,51 @@ struct DtUser {
     double *u[MAX_BLOCKS];
 };
 
+// Per-cell spectral radius sum_d (|u . Sbar_d| + c |Sbar_d|) and |Omega| in
+// the arithmetic type R: FP64 on the FP64 metrics, or FP32 (the
+// mixed-precision modes) on their FP32 copies.
+template <typename R>
+struct DtMath;
+template <>
+struct DtMath<double> {
+    static __device__ __forceinline__ double cv(double x) { return x; }
+    static __device__ __forceinline__ double rcp(double x) { return rcp_exact(x); }
+    static __device__ __forceinline__ double rsqrt(double x) { return rsqrt_exact(x); }
+    static __device__ __forceinline__ double sb(const BlockDev &B, long long q) { return B.sbar[q]; }
+    static __device__ __forceinline__ double vol(const BlockDev &B, long long m) { return B.vol[m]; }
+};
+template <>
+struct DtMath<float> {
+    static __device__ __forceinline__ float cv(double x) { return __double2float_rn(x); }
+    static __device__ __forceinline__ float rcp(float x)
+    {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float rsqrt(float x)
+    {
+        float r;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float sb(const BlockDev &B, long long q) { return B.sbar32[q]; }
+    static __device__ __forceinline__ float vol(const BlockDev &B, long long m) { return B.vol32[m]; }
+};
+
 // One CTA per work item (tile column x k-chunk of one block), grid-stride
 // over the items; each thread walks its column.
+template <typename R>
 __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, int nblocks, long long nitems,
                                                       const __grid_constant__ DtUser user, double gamma,
                                                       int local, double cfl, unsigned long long *dt_bits,
                                                       unsigned *err)
 {
+    using M = DtMath<R>;
     const int t = threadIdx.x;
     const int ti = t % TI, tj = t / TI;
-    double best = INFINITY;
+    const R gam = (R)gamma, gm1 = (R)(gamma - 1.0);
+    R best = R(INFINITY);
     bool bad = false;
     for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int b = find_block_item(blocks, nblocks, item);
@@ -65,37 +101,39 @@ __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, in
         const long long mv = B.ml.mvolume;
         for (int k = k0; k < k1; ++k) {
             const double *c = U + cell_index(B.L, i, j, k);
-            double rho = c[0], mx = c[B.L.sv], my = c[2 * B.L.sv], mz = c[3 * B.L.sv], E = c[4 * B.L.sv];
-            double ir = rcp_exact(rho);
-            double u = mx * ir, v = my * ir, w = mz * ir;
-            double p = (gamma - 1.0) * (E - 0.5 * (mx * u + my * v + mz * w));
-            if (!(rho > 0.0 && p > 0.0 && rho < INFINITY && p < INFINITY)) {
+            const R rho = M::cv(c[0]), mx = M::cv(c[B.L.sv]), my = M::cv(c[2 * B.L.sv]), mz = M::cv(c[3 * B.L.sv]),
+                    E = M::cv(c[4 * B.L.sv]);
+            const R ir = M::rcp(rho);
+            const R u = mx * ir, v = my * ir, w = mz * ir;
+            const R p = gm1 * (E - R(0.5) * (mx * u + my * v + mz * w));
+            if (!(rho > R(0) && p > R(0) && rho < R(INFINITY) && p < R(INFINITY))) {
                 bad = true;
                 continue;
             }
-            const double a2 = gamma * p * ir;
-            const double a = a2 * rsqrt_exact(a2);
+            const R a2 = gam * p * ir;
+            const R a = a2 * M::rsqrt(a2);
             const long long m = k * B.ml.mplane + j * B.ml.mpitch + i;
-            double sum = 0.0;
+            R sum = R(0);
             for (int d = 0; d < ndir; ++d) {
-                const double *sb = B.sbar + (long long)(d * 4) * mv;
-                double un = u * sb[m] + v * sb[mv + m] + w * sb[2 * mv + m];
-                sum += fabs(un) + a * sb[3 * mv + m];
+                const long long q = (long long)(d * 4) * mv + m;
+                const R un = u * M::sb(B, q) + v * M::sb(B, mv + q) + w * M::sb(B, 2 * mv + q);
+                sum += fabs(un) + a * M::sb(B, 3 * mv + q);
             }
-            const double isum = rcp_exact(sum);
-            if (local) B.dtv[m] = cfl * isum;
-            best = fmin(best, B.vol[m] * isum);
+            const R isum = M::rcp(sum);
+            if (local) B.dtv[m] = cfl * (double)isum;
+            best = fmin(best, M::vol(B, m) * isum);
         }
     }
     if (bad) atomicOr(err, ERR_NONPHYSICAL);
+    double bestd = (double)best;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
+    for (int o = 16; o > 0; o >>= 1) bestd = fmin(bestd, __shfl_down_sync(0xffffffffu, bestd, o));
     __shared__ double red[NTHREADS / 32];
-    if ((t & 31) == 0) red[t >> 5] = best;
+    if ((t & 31) == 0) red[t >> 5] = bestd;
     __syncthreads();
     if (t == 0) {
-        for (int w = 1; w < NTHREADS / 32; ++w) best = fmin(best, red[w]);
-        if (best < INFINITY) atomicMin(dt_bits, (unsigned long long)__double_as_longlong(best));
+        for (int w = 1; w < NTHREADS / 32; ++w) bestd = fmin(bestd, red[w]);
+        if (bestd < INFINITY) atomicMin(dt_bits, (unsigned long long)__double_as_longlong(bestd));
     }
 }
 
@@ -128,11 +166,15 @@ __global__ void norms_finalize_kernel(const double *__restrict__ partials, int n
 }  // namespace
 
 cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
-                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, cudaStream_t s)
+                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, bool fp32,
+                      cudaStream_t s)
 {
     DtUser u;
     for (int b = 0; b < nblocks; ++b) u.u[b] = user[b];
-    dt_kernel<<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, local, cfl, dt_bits, err);
+    if (fp32)
+        dt_kernel<float><<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, local, cfl, dt_bits, err);
+    else
+        dt_kernel<double><<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, local, cfl, dt_bits, err);
     return cudaGetLastError();
 }
 

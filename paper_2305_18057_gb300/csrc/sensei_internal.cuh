@@ -59,6 +59,7 @@ struct MetricsOut {
     double *n[3][4];
     double *vol, *ivol;
     double *sbar[3][4];
+    float *sbar32[3][4], *vol32;   // may be null
 };
 
 // ------------------------------------------------------------------------
@@ -80,6 +81,7 @@ struct BlockDev {
     const float *rec32;     // FP32 face-metric records of the FP32 stencil (null in FP64 mode)
     const double *vol, *ivol;
     const double *sbar;     // spectral metrics: 12 arrays of mvolume, index (direction*4 + q)
+    const float *sbar32, *vol32;   // their FP32 copies and |Omega| in FP32 (null in FP64 mode)
     double *dtv;            // local time stepping: dt_c / |Omega| per cell (mvolume)
     double *st64[2];        // FP64 stage states
     float *xs[2], *ds[2];   // FP32 stage states and increments
@@ -162,8 +164,10 @@ int stencil_ctas_per_sm_f32(int precision_kind, int limiter, bool two_d);
 int stencil_ctas_per_sm_f32s(int limiter, bool two_d);
 // min over cells of |Omega| / sum_d (|u.Sbar_d| + c |Sbar_d|) into dt_bits; with local set,
 // also dtv = cfl / sum_d (...) = dt_c / |Omega| per cell
+// fp32: FP32 arithmetic on the FP32 metric copies (the mixed-precision modes)
 cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
-                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, cudaStream_t s);
+                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, bool fp32,
+                      cudaStream_t s);
 cudaError_t launch_set_scalar(double *slot, double v, cudaStream_t s);
 cudaError_t launch_scale_copy(double *dst, const double *src, double scale, cudaStream_t s);
 // Record the thread-local message returned by sensei_last_error (api.cu).
