@@ -68,30 +68,25 @@ def alg_flops_per_cell(limiter, two_d, alpha_nonzero, first_stage):
 def alg_bytes_per_cell(form, stage, two_d, stages=3):
     """Bytes the stencil kernel must move per interior cell in the launch of
     RK stage `stage` (0-based) of an SSPRK3 step:
-      fp64 / fp32_flux: read U^(s-1) (40), write U^(s) (40), read U^n on the
-        stages that blend it (40), face metrics (unit normal + area of the
-        nd low faces: 32 B each in FP64, 16 B in FP32) and 1/|Omega| (8),
-        |Omega| (8) for the conservation sums on the first stage;
-      fp32_store: first stage reads U (40) and writes D, X (20 + 20); middle
-        stages read X (20), D (20), U^n (40) and write D, X (40); the last
-        reads X, D (40) and U^n (40) and writes U (40); FP32 face metrics and
-        1/|Omega| (4), |Omega| (8) on the first stage."""
+      fp64: read U^(s-1) (40), write U^(s) (40), read U^n on the stages that
+        blend it (40), FP64 face metrics (unit normal + area of the nd low
+        faces, 32 B each) and 1/|Omega| (8), |Omega| (8) for the
+        conservation sums on the first stage;
+      fp32_flux: the same state bytes; the FP32 face-metric record of the
+        tile-plane (13,952 B per 256 cells = 54.5 B, with 1/|Omega| in FP32)
+        and the FP64 1/|Omega| (8) of the FP64 update;
+      fp32_store: the record (54.5); first stage reads U (40) and writes D,
+        X (20 + 20) and reads |Omega| (8); later stages read X (20), D (20),
+        U^n (40) and write D, X (40) or, on the last, U (40)."""
     nd = 2 if two_d else 3
+    rec = 13952.0 / 256.0
     if form == "fp32_store":
-        b = nd * 16 + 4
-        if stage == 0:
-            b += 40 + 40 + 8
-        elif stage == stages - 1:
-            b += 40 + 40 + 40
-        else:
-            b += 40 + 40 + 40
-        return b
-    mbytes = 16 if form == "fp32_flux" else 32
-    b = 40 + 40 + nd * mbytes + 8
-    if stage > 0:
-        b += 40
+        return rec + (40 + 40 + 8 if stage == 0 else 40 + 40 + 40)
+    if form == "fp32_flux":
+        b = 40 + 40 + rec + 8
     else:
-        b += 8
+        b = 40 + 40 + nd * 32 + 8
+    b += 40 if stage > 0 else 8
     return b
 
 
