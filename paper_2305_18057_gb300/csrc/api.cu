@@ -368,6 +368,12 @@ void fill_params(BatchParams<R> &p, const sensei_grid *g, const StencilCall &c)
     p.kappa = (R)g->scheme.kappa;
     p.eps = (R)g->scheme.eps;
     p.fix = (R)g->scheme.entropy_fix;
+    // the derived constants, in R arithmetic as the kernels would form them
+    p.gm1 = p.gamma - (R)1;
+    p.kg = p.gamma / p.gm1;
+    p.c1 = p.eps * ((R)1 - p.kappa) * (R)0.25;
+    p.c2 = p.eps * ((R)1 + p.kappa) * (R)0.25;
+    p.half_eps = (R)0.5 * p.eps;
     p.cons = g->scheme.reconstruct_conserved ? 1 : 0;
     p.alpha = c.alpha;
     p.beta = c.beta;

@@ -122,6 +122,7 @@ struct BatchParams {
     int push;
     int local;              // local time stepping: the stage step is dtv[cell], not dt / |Omega|
     R gamma, kappa, eps, fix;
+    R gm1, kg, c1, c2, half_eps;   // gamma - 1, gamma / (gamma - 1), eps (1 -+ kappa) / 4, eps / 2 in R
     int cons;
     double alpha, beta, gdt;
     const double *dt_slot;  // dt = dt_scale * *dt_slot

@@ -40,16 +40,20 @@ static_assert(TI == 32, "one warp per tile row");
 
 template <typename TS>
 struct Smem32 {
-    // raw[2][NV][TH][TW] TS | met[2][REC] | W[NV][TH][TW] | Fi[NV][TJ][TI+1] |
-    // Fj[NV][TJ+1][TI] | reduction scratch | two mbarriers
+    // raw[2][NV][TH][TW] TS | met[2][REC] | W[NV][TH][TW] | Fj[NV][TJ+1][TI] |
+    // FiE[NV][TJ] (the tile's right i-faces) | K[3][NV][NTHREADS] (own column:
+    // planes k+1 and k+2, the flux of the lower k-face) | reduction scratch
+    // (FP64 input only) | two mbarriers
     static constexpr size_t raw_buf = (size_t)NV * TPLANE * sizeof(TS);
     static constexpr size_t off_raw = 0;
     static constexpr size_t off_met = off_raw + 2 * raw_buf;
     static constexpr size_t off_w = off_met + 2 * (size_t)REC * sizeof(float);
-    static constexpr size_t off_fi = off_w + (size_t)NV * TPLANE * sizeof(float);
-    static constexpr size_t off_fj = off_fi + (size_t)NV * TJ * (TI + 1) * sizeof(float);
-    static constexpr size_t off_red = (off_fj + (size_t)NV * (TJ + 1) * TI * sizeof(float) + 15) / 16 * 16;
-    static constexpr size_t off_bar = off_red + 3 * NV * (NTHREADS / 32) * sizeof(double);
+    static constexpr size_t off_fj = off_w + (size_t)NV * TPLANE * sizeof(float);
+    static constexpr size_t off_fie = off_fj + (size_t)NV * (TJ + 1) * TI * sizeof(float);
+    static constexpr size_t off_k = off_fie + (size_t)NV * TJ * sizeof(float);
+    static constexpr size_t off_red = (off_k + 3 * (size_t)NV * NTHREADS * sizeof(float) + 15) / 16 * 16;
+    static constexpr size_t red_bytes = sizeof(TS) == 8 ? 3 * NV * (NTHREADS / 32) * sizeof(double) : 0;
+    static constexpr size_t off_bar = off_red + red_bytes;
     static constexpr size_t bytes = off_bar + 2 * sizeof(unsigned long long);
     static_assert(raw_buf % 16 == 0 && off_met % 16 == 0, "bulk-copy destinations are 16-byte aligned");
     static_assert((TW * sizeof(TS)) % 16 == 0, "tile rows are 16-byte aligned");
@@ -134,6 +138,8 @@ __device__ __forceinline__ void issue_plane(const TS *in, const StateLayout &L, 
 
 // ---- FP32 helpers -----------------------------------------------------------
 
+__device__ __forceinline__ void prefetch_l2(const void *ptr) { asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr)); }
+
 // raw loads of one cell of the own column (no conversion: the value is
 // consumed planes later, so the load latency stays hidden)
 template <typename TS>
@@ -184,7 +190,7 @@ __device__ __forceinline__ void ds_add(float &s_hi, float &s_lo, float hi, float
 }
 
 template <typename TS, int LIM, bool TWO_D>
-__global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_constant__ BatchParams<float> p)
+__global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_kernel(const __grid_constant__ BatchParams<float> p)
 {
     using SM = Smem32<TS>;
     constexpr bool WIDE = sizeof(TS) == 8;   // FP64 stage input: the only case that computes norms
@@ -192,13 +198,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
     TS *sRaw = reinterpret_cast<TS *>(smem + SM::off_raw);
     float *sMet = reinterpret_cast<float *>(smem + SM::off_met);
     float *sW = reinterpret_cast<float *>(smem + SM::off_w);
-    float *sFi = reinterpret_cast<float *>(smem + SM::off_fi);
     float *sFj = reinterpret_cast<float *>(smem + SM::off_fj);
+    float *sFiE = reinterpret_cast<float *>(smem + SM::off_fie);
+    float *sK = reinterpret_cast<float *>(smem + SM::off_k);
     double *sRed = reinterpret_cast<double *>(smem + SM::off_red);
     const uint32_t bar0 = smem_addr(smem + SM::off_bar);
     __shared__ BlockDev sB;
 
-    constexpr int FIV = TJ * (TI + 1);   // sFi variable plane
     constexpr int FJV = (TJ + 1) * TI;   // sFj variable plane
     constexpr int NFACES = TWO_D ? 4 : 6;
 
@@ -206,13 +212,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
     const int lane = t & 31, warp = t >> 5;
     const int ti = lane, tj = warp;
 
-    const float gm1 = p.gamma - 1.0f;
-    const float kg = p.gamma / gm1;
-    const float c1 = p.eps * (1.0f - p.kappa) * 0.25f;
-    const float c2 = p.eps * (1.0f + p.kappa) * 0.25f;
-    const float half_eps = 0.5f * p.eps;
-    const float fix = p.fix;
-    const int cons = p.cons;
+    // scheme constants straight from the parameter bank (no registers held)
+#define gm1 p.gm1
+#define kg p.kg
+#define c1 p.c1
+#define c2 p.c2
+#define half_eps p.half_eps
+#define fix p.fix
+#define cons p.cons
     const bool update = p.mode != MODE_RESIDUAL;
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
     const float gdt_dt32 = (float)(p.gdt * dt);
@@ -253,11 +260,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
         const TS *in = (p.in_slot == SLOT_X0 || p.in_slot == SLOT_X1)
                            ? reinterpret_cast<const TS *>(slot32(B, p.in_slot))
                            : reinterpret_cast<const TS *>(slot64(B, p.user[b], p.in_slot));
-        const double *un = p.user[b];
-        double *out64 = (p.mode != MODE_RESIDUAL && p.out_slot < SLOT_X0) ? slot64(B, p.user[b], p.out_slot) : nullptr;
-        float *xout = (p.mode == MODE_INCR && p.out_slot >= SLOT_X0) ? slot32(B, p.out_slot) : nullptr;
-        const float *dprev = p.dprev >= 0 ? B.ds[p.dprev] : nullptr;
-        float *dout = p.dout >= 0 ? B.ds[p.dout] : nullptr;
+        // the update's pointers, formed from the descriptor in shared memory
+        // where they are used (not held in registers through the fluxes)
+        const bool out_wide = p.mode != MODE_RESIDUAL && p.out_slot < SLOT_X0;
         const int nrows = min(TH, B.nj + 4 - j0);
         const int len = min(TW, (int)L.sj - i0);
         const long long rec_stride = (long long)B.tiles_i * B.tiles_j * REC;
@@ -280,7 +285,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
         }
 
         // own-column k-window (3D)
-        float Wc[NV], W1[NV], W2[NV], Pp[NV], Fkm[NV];
+        // sK[kb] holds plane k+1 of the own column, sK[kb ^ 1] plane k+2
+        // (each thread touches only its own entries)
+        int kb = 0;
+        float *sFkm = sK + 2 * NV * NTHREADS;   // [NV][NTHREADS]: the own column's lower k-face flux
+        float Wc[NV], Pp[NV];
         TS pre[NV];
         if (!TWO_D) {
             TS q[NV];
@@ -300,11 +309,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
             load_cell<TS>(in, L, B.ni, B.nj, B.nk, ci, cj, k0 + 1, q);
 #pragma unroll
             for (int v = 0; v < NV; ++v) qf[v] = cvt<float, TS>(q[v]);
+            float W1[NV], W2[NV];
             to_recon(qf, gm1, cons, col_valid && k0 + 1 < B.nk, p.err, W1);
             load_cell<TS>(in, L, B.ni, B.nj, B.nk, ci, cj, k0 + 2, q);
 #pragma unroll
             for (int v = 0; v < NV; ++v) qf[v] = cvt<float, TS>(q[v]);
             to_recon(qf, gm1, cons, col_valid && k0 + 2 < B.nk, p.err, W2);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                sK[(0 * NV + v) * NTHREADS + t] = W1[v];
+                sK[(1 * NV + v) * NTHREADS + t] = W2[v];
+            }
             float Lk[NV], Rk[NV], unused;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -314,29 +329,25 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
             // the k0 - 1/2 face, from the FP64 metrics
             const long long fk = (long long)k0 * ml.mplane + (long long)min(cj, B.nj - 1) * ml.mpitch + min(ci, B.ni - 1);
             const double *f2 = B.fn + 8 * ml.mvolume;
+            float Fkm[NV];
             face_flux(Lk, Rk, to_f32(f2[fk]), to_f32(f2[ml.mvolume + fk]), to_f32(f2[2 * ml.mvolume + fk]),
                       to_f32(f2[3 * ml.mvolume + fk]), gm1, kg, fix, cons, Fkm);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sFkm[v * NTHREADS + t] = Fkm[v];
         }
 
         for (int k = k0; k < k1; ++k) {
             if (!TWO_D) load_cell<TS>(in, L, B.ni, B.nj, B.nk, ci, cj, k + 3, pre);
-            const long long kpl = (long long)k * ml.mplane;
-            const long long cell = L.off + (long long)k * L.sk + (long long)cj * L.sj + ci;
-            const long long mc = kpl + (long long)cj * ml.mpitch + ci;
-            // per-cell operands of the update, loaded now and used after the fluxes
-            double unv[NV];
-            float dpv[NV];
-            double ivd = 0.0, vold = 0.0, dtvd = 0.0;
-            const bool need_un = (p.mode == MODE_ACCUM && p.alpha != 0.0) || (p.mode == MODE_INCR && (out64 || !WIDE));
+            const bool need_un = (p.mode == MODE_ACCUM && p.alpha != 0.0) || (p.mode == MODE_INCR && (out_wide || !WIDE));
             if (col_valid) {
+                // warm L2 with the update's per-cell operands; they are loaded
+                // after the fluxes
+                const long long cell = L.off + (long long)k * L.sk + (long long)cj * L.sj + ci;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    unv[v] = need_un ? un[cell + v * L.sv] : 0.0;
-                    dpv[v] = dprev ? dprev[cell + v * L.sv] : 0.0f;
+                    if (need_un) prefetch_l2(p.user[b] + cell + v * L.sv);
+                    if (p.dprev >= 0) prefetch_l2(B.ds[p.dprev] + cell + v * L.sv);
                 }
-                if (p.local) dtvd = B.dtv[mc];
-                else if (p.mode == MODE_ACCUM) ivd = B.ivol[mc];
-                if (WIDE && p.partials) vold = B.vol[mc];
             }
 
             // ---- P0: wait for the plane's tile, primitives into sW
@@ -401,24 +412,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
                                     sRaw + nb * NV * TPLANE, sMet + nb * REC, bar0 + 8 * nb, lane);
             }
 
-            // ---- P1: fluxes: the own column's upper k-face (registers), the
-            //      i-face left of the own cell, the j-face below it; warp 0
-            //      also the tile's top j-faces, warp 1 its right i-faces
-            float Fkp[NV], Ppn[NV];
-            if (!TWO_D) {
-                float Rk[NV];
-#pragma unroll
-                for (int v = 0; v < NV; ++v)
-                    face_states<float, LIM>(Wc[v], W1[v], W2[v], c1, c2, half_eps, Ppn[v], Rk[v]);
-                const float *mk = met + REC_I + REC_J + tj * TI + ti;
-                face_flux(Pp, Rk, mk[0], mk[TJ * TI], mk[2 * TJ * TI], mk[3 * TJ * TI], gm1, kg, fix, cons, Fkp);
-            }
+            // ---- P1: fluxes: the j-face below the own cell (to sFj); warp 0
+            //      also the tile's top j-faces, warp 1 its right i-faces (to
+            //      sFiE); the own column's upper k-face and the i-face left
+            //      of the own cell stay in registers
             {
                 float F[NV];
-                line_flux<LIM>(sW + (tj + 2) * TW + ti, 1, met + tj * (TI + 1) + ti, TJ * (TI + 1), gm1, kg, fix, c1,
-                               c2, half_eps, cons, F);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sFi[v * FIV + tj * (TI + 1) + ti] = F[v];
                 line_flux<LIM>(sW + tj * TW + ti + 2, TW, met + REC_I + tj * TI + ti, (TJ + 1) * TI, gm1, kg, fix,
                                c1, c2, half_eps, cons, F);
 #pragma unroll
@@ -432,19 +431,56 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
                     line_flux<LIM>(sW + (lane + 2) * TW + TI, 1, met + lane * (TI + 1) + TI, TJ * (TI + 1), gm1, kg,
                                    fix, c1, c2, half_eps, cons, F);
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) sFi[v * FIV + lane * (TI + 1) + TI] = F[v];
+                    for (int v = 0; v < NV; ++v) sFiE[v * TJ + lane] = F[v];
                 }
             }
+            float Fkp[NV], Ppn[NV];
+            if (!TWO_D) {
+                float Rk[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+                    face_states<float, LIM>(sW[v * TPLANE + (tj + 2) * TW + ti + 2], sK[(kb * NV + v) * NTHREADS + t],
+                                            sK[((kb ^ 1) * NV + v) * NTHREADS + t], c1, c2, half_eps, Ppn[v], Rk[v]);
+                const float *mk = met + REC_I + REC_J + tj * TI + ti;
+                face_flux(Pp, Rk, mk[0], mk[TJ * TI], mk[2 * TJ * TI], mk[3 * TJ * TI], gm1, kg, fix, cons, Fkp);
+            }
+            float Fi[NV];
+            line_flux<LIM>(sW + (tj + 2) * TW + ti, 1, met + tj * (TI + 1) + ti, TJ * (TI + 1), gm1, kg, fix, c1, c2,
+                           half_eps, cons, Fi);
             __syncthreads();
 
             // ---- P2: residual, update, ghost push, norm partials
+            // the i-face right of the own cell: the next lane's, or for lane
+            // 31 the tile's right face (all lanes take part in the shuffle)
+            float Fr[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                Fr[v] = __shfl_down_sync(0xffffffffu, Fi[v], 1);
+                if (lane == TI - 1) Fr[v] = sFiE[v * TJ + tj];
+            }
             if (col_valid) {
+                const long long cell = L.off + (long long)k * L.sk + (long long)cj * L.sj + ci;
+                const long long mc = (long long)k * ml.mplane + (long long)cj * ml.mpitch + ci;
+                const double *un = p.user[b];
+                const float *dprev = p.dprev >= 0 ? B.ds[p.dprev] : nullptr;
+                double unv[NV];
+                float dpv[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    unv[v] = need_un ? un[cell + v * L.sv] : 0.0;
+                    dpv[v] = dprev ? dprev[cell + v * L.sv] : 0.0f;
+                }
+                const double dtvd = p.local ? B.dtv[mc] : 0.0;
+                const double ivd = (!p.local && p.mode == MODE_ACCUM) ? B.ivol[mc] : 0.0;
+                const double vold = (WIDE && p.partials) ? B.vol[mc] : 0.0;
+                double *out64 = out_wide ? slot64(B, p.user[b], p.out_slot) : nullptr;
+                float *xout = (p.mode == MODE_INCR && p.out_slot >= SLOT_X0) ? slot32(B, p.out_slot) : nullptr;
+                float *dout = p.dout >= 0 ? B.ds[p.dout] : nullptr;
                 float rres[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    float rr = (sFi[v * FIV + tj * (TI + 1) + ti + 1] - sFi[v * FIV + tj * (TI + 1) + ti]) +
-                               (sFj[v * FJV + (tj + 1) * TI + ti] - sFj[v * FJV + tj * TI + ti]);
-                    if (!TWO_D) rr += Fkp[v] - Fkm[v];
+                    float rr = (Fr[v] - Fi[v]) + (sFj[v * FJV + (tj + 1) * TI + ti] - sFj[v * FJV + tj * TI + ti]);
+                    if (!TWO_D) rr += Fkp[v] - sFkm[v * NTHREADS + t];
                     rres[v] = rr;
                 }
                 const int e_own = (tj + 2) * TW + ti + 2;
@@ -522,13 +558,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
                 float qf[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    Fkm[v] = Fkp[v];
+                    sFkm[v * NTHREADS + t] = Fkp[v];
                     Pp[v] = Ppn[v];
-                    Wc[v] = W1[v];
-                    W1[v] = W2[v];
+                    Wc[v] = sK[(kb * NV + v) * NTHREADS + t];
                     qf[v] = cvt<float, TS>(pre[v]);
                 }
-                to_recon(qf, gm1, cons, col_valid && k + 3 < B.nk, p.err, W2);
+                float w3[NV];
+                to_recon(qf, gm1, cons, col_valid && k + 3 < B.nk, p.err, w3);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sK[(kb * NV + v) * NTHREADS + t] = w3[v];
+                kb ^= 1;
             }
             cb ^= 1;
         }
@@ -563,6 +602,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32_kernel(const __grid_con
             }
         }
     }
+#undef gm1
+#undef kg
+#undef c1
+#undef c2
+#undef half_eps
+#undef fix
+#undef cons
 }
 
 template <typename TS>
