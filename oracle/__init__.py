@@ -1,4 +1,5 @@
-"""Plain FP64 CPU oracle for the SENSEI explicit residual + Runge-Kutta path.
+"""Plain FP64 CPU oracle for the SENSEI explicit residual + Runge-Kutta path
+(Euler, or Navier-Stokes with mu > 0).
 
 TEST INFRASTRUCTURE.  The oracle restates arXiv 2305.18057 Sec. 2-3 and the
 MUSCL paragraph of Sec. 5 in plain C (``sensei_oracle.c``, IEEE double,
@@ -76,6 +77,7 @@ def lib():
             L.ora_rk_step_local.restype = C.c_double
             L.ora_rk_step_local.argtypes = [C.c_void_p, C.POINTER(_dp), C.POINTER(_dp), C.c_int, C.c_double, _dp]
             L.ora_rk_tableau.argtypes = [C.c_int, _dp, _dp, C.POINTER(C.c_int)]
+            L.ora_set_viscosity.argtypes = [C.c_void_p, C.c_double, C.c_double]
             L.ora_euler_flux.argtypes = [C.c_double, _dp, _dp, _dp]
             L.ora_roe_flux.argtypes = [C.c_double, C.c_double, _dp, _dp, _dp, _dp]
             L.ora_roe_jump.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
@@ -170,7 +172,7 @@ class OracleGrid:
     """Multiblock structured grid held by the oracle (metrics computed in C)."""
 
     def __init__(self, dims, nodes, gamma=1.4, limiter=LIM_VANLEER, kappa=1.0 / 3.0, eps=1.0,
-                 recon_conserved=False, fix=0.1):
+                 recon_conserved=False, fix=0.1, mu=0.0, prandtl=0.72):
         self.dims = [tuple(int(v) for v in d) for d in dims]
         self.nodes = [np.ascontiguousarray(x, dtype=np.float64) for x in nodes]
         for (ni, nj, nk), X in zip(self.dims, self.nodes):
@@ -178,7 +180,9 @@ class OracleGrid:
         flat = (C.c_int * (3 * len(self.dims)))(*[v for d in self.dims for v in d])
         self._h = lib().ora_create(len(self.dims), flat, _ptrs(self.nodes), gamma, limiter, kappa,
                                    eps, int(recon_conserved), fix)
+        lib().ora_set_viscosity(self._h, mu, prandtl)
         self.gamma = gamma
+        self.mu, self.prandtl = mu, prandtl
 
     def __del__(self):
         h = getattr(self, "_h", None)

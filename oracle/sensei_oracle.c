@@ -58,6 +58,7 @@ typedef struct {
     double kappa, eps;
     int recon_conserved;
     double fix_delta;                /* Harten entropy-fix width, times the Roe sound speed */
+    double mu, prandtl;              /* viscous flux F_nu (mu = 0: Euler) */
 } ora_grid;
 
 /* ------------------------------------------------------------------------ */
@@ -455,7 +456,14 @@ static void boundary_normal(const ora_block *b, int f, int t1, int t2, double n[
     n[2] = S[2] / area;
 }
 
-static void fill_face(const ora_grid *g, int bi, int f, double *const *U)
+/* Ghost cells of face f.  edges = 0: the face's own ghosts (tangential
+ * positions inside the face).  edges = 1: the block-edge ghosts the viscous
+ * face gradients read (two indices outside the block), filled after every
+ * face's own ghosts by the rule of the lower face family: an i-face fills
+ * its ghosts at j- or k-ghost positions, a j-face those at k-ghost
+ * positions; the rule then reads ghosts of the other family (its own
+ * block's, or for an interface the neighbour's), already in place. */
+static void fill_face_range(const ora_grid *g, int bi, int f, double *const *U, int edges)
 {
     const ora_block *b = &g->b[bi];
     double *u = U[bi];
@@ -464,8 +472,14 @@ static void fill_face(const ora_grid *g, int bi, int f, double *const *U)
     int type = b->bc_type[f];
     double Qinf[NV];
     if (type == ORA_BC_INFLOW) prim_to_cons(g->gamma, b->bc_prim[f], Qinf);
-    for (int t2 = 0; t2 < n2; ++t2)
-        for (int t1 = 0; t1 < n1; ++t1)
+    /* the tangential ranges: the second tangential index has no ghosts in 2D */
+    int fam = f >> 1;
+    int g1 = edges && fam == 0 ? NG : 0;                       /* t1 = j for i-faces, i otherwise */
+    int g2 = edges && fam < 2 && !is2d(b) ? NG : 0;           /* t2 = k for i- and j-faces */
+    for (int t2 = -g2; t2 < n2 + g2; ++t2)
+        for (int t1 = -g1; t1 < n1 + g1; ++t1) {
+            int out1 = t1 < 0 || t1 >= n1, out2 = t2 < 0 || t2 >= n2;
+            if (edges ? (out1 + out2 != 1) : (out1 || out2)) continue;
             for (int layer = 1; layer <= NG; ++layer) {
                 long gc = ghost_cell(b, f, layer, t1, t2);
                 if (type == ORA_BC_PERIODIC) {
@@ -481,10 +495,12 @@ static void fill_face(const ora_grid *g, int bi, int f, double *const *U)
                 } else if (type == ORA_BC_SLIP_WALL) {
                     /* mirror image of the interior cell layer-1 cells inside:
                      * density and total energy copied, momentum reflected,
-                     * m_g = m - 2 (m . n) n */
+                     * m_g = m - 2 (m . n) n (at an edge, n of the nearest
+                     * boundary face) */
                     long src = inner_cell(b, f, layer - 1, t1, t2);
                     double n[3];
-                    boundary_normal(b, f, t1, t2, n);
+                    boundary_normal(b, f, t1 < 0 ? 0 : (t1 >= n1 ? n1 - 1 : t1), t2 < 0 ? 0 : (t2 >= n2 ? n2 - 1 : t2),
+                                    n);
                     double m[3] = {u[1 * b->sv + src], u[2 * b->sv + src], u[3 * b->sv + src]};
                     double mn = m[0] * n[0] + m[1] * n[1] + m[2] * n[2];
                     u[0 * b->sv + gc] = u[0 * b->sv + src];
@@ -502,11 +518,14 @@ static void fill_face(const ora_grid *g, int bi, int f, double *const *U)
                     for (int q = 0; q < NV; ++q) u[q * b->sv + gc] = un[q * nb->sv + src];
                 }
             }
+        }
 }
 
+static void fill_face(const ora_grid *g, int bi, int f, double *const *U) { fill_face_range(g, bi, f, U, 0); }
+
 /* ------------------------------------------------------------------------ */
-/* residual, Eq. residual: R_h = sum over the f faces of F_{i,n} Delta s     */
-/*                               - |Omega| S_h                               */
+/* residual, Eq. residual: R_h = sum over the f faces of                     */
+/*                               (F_{i,n} - F_{nu,n}) Delta s - |Omega| S_h  */
 /* with R taken on the outward area vector of each face, so that            */
 /* |Omega| dU/dt = -R (Eq. spatial_residual).                                */
 /* ------------------------------------------------------------------------ */
@@ -540,6 +559,150 @@ static void stencil_flux(const ora_grid *g, const ora_block *b, const double *u,
     roe_flux(g->gamma, g->fix_delta, WL, WR, S, F);
 }
 
+/* ------------------------------------------------------------------------ */
+/* viscous flux F_nu,n of Eq. governing (Stokes's hypothesis; Theta = work  */
+/* of the viscous stresses + heat conduction).  The paper gives neither the */
+/* viscosity law nor the face-gradient discretisation; the readings used:   */
+/* constant mu, heat conductivity mu c_p / Pr (so that k grad T =            */
+/* mu gamma / ((gamma - 1) Pr) grad(p / rho)), and face gradients from      */
+/* computational-space central differences and the metric identity         */
+/* grad xi_a = Sbar_a / |Omega|, both averaged over the face's two cells.   */
+/* ------------------------------------------------------------------------ */
+
+/* the viscous variables (u, v, w, p / rho) of a ghosted cell */
+static void vis_vars(const ora_grid *g, const ora_block *b, const double *u, int i, int j, int k, double phi[4])
+{
+    double Q[NV], W[NV];
+    long c0 = cell(b, i, j, k);
+    for (int q = 0; q < NV; ++q) Q[q] = u[q * b->sv + c0];
+    cons_to_prim(g->gamma, Q, W);
+    phi[0] = W[1];
+    phi[1] = W[2];
+    phi[2] = W[3];
+    phi[3] = W[4] / W[0];
+}
+
+/* area vector of face family a at face index (i, j, k) (lowest-corner) */
+static void face_vector(const ora_block *b, int a, int i, int j, int k, double S[3])
+{
+    for (int c = 0; c < 3; ++c) {
+        if (a == 0) S[c] = b->Si[c * n_fi(b) + fi_index(b, i, j, k)];
+        else if (a == 1) S[c] = b->Sj[c * n_fj(b) + fj_index(b, i, j, k)];
+        else S[c] = b->Sk[c * n_fk(b) + fk_index(b, i, j, k)];
+    }
+}
+
+/* Sbar_a of interior cell (i, j, k): the mean of its two a-face vectors */
+static void cell_sbar(const ora_block *b, int a, int i, int j, int k, double S[3])
+{
+    double s0[3], s1[3];
+    face_vector(b, a, i, j, k, s0);
+    face_vector(b, a, i + (a == 0), j + (a == 1), k + (a == 2), s1);
+    for (int c = 0; c < 3; ++c) S[c] = 0.5 * (s0[c] + s1[c]);
+}
+
+static int clampi(int x, int n) { return x < 0 ? 0 : (x >= n ? n - 1 : x); }
+
+/* The cell whose geometry a cell of a face stencil carries: an interior
+ * cell its own; a ghost cell (outside in one direction) that of the cell it
+ * copies -- the opposite side's cell for a periodic face, the neighbour
+ * block's cell for an interface -- or, behind a physical boundary, the
+ * boundary cell it mirrors. */
+static const ora_block *metric_cell(const ora_grid *g, const ora_block *b, int c[3])
+{
+    int n[3] = {b->ni, b->nj, b->nk};
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] >= 0 && c[a] < n[a]) continue;
+        int hi = c[a] >= n[a];
+        int f = 2 * a + hi;
+        int layer = hi ? c[a] - n[a] + 1 : -c[a];     /* 1 next to the boundary */
+        int type = b->bc_type[f];
+        if (type == ORA_BC_PERIODIC) {
+            c[a] = hi ? c[a] - n[a] : c[a] + n[a];
+        } else if (type == ORA_BC_INTERFACE) {
+            const ora_block *nb = &g->b[b->bc_nbr[f]];
+            int nf = b->bc_nbr_face[f];
+            int m[3] = {nb->ni, nb->nj, nb->nk};
+            c[a] = (nf & 1) ? m[a] - layer : layer - 1;
+            return nb;
+        } else {
+            c[a] = clampi(c[a], n[a]);
+        }
+    }
+    return b;
+}
+
+/* F_nu . S through the d-face between cells L = (i, j, k) - e_d and
+ * R = (i, j, k) (face index (i, j, k), area vector S toward +d). */
+static void viscous_flux(const ora_grid *g, const ora_block *b, const double *u, int d, int i, int j, int k,
+                         const double S[3], double F[NV])
+{
+    int ndir = is2d(b) ? 2 : 3;
+    int L[3] = {i - (d == 0), j - (d == 1), k - (d == 2)};
+    int R[3] = {i, j, k};
+    /* the tangential families e, f of direction d */
+    int e = d == 0 ? 1 : 0;
+    int f = d == 2 ? 1 : 2;
+    double pL[4], pR[4], dxi[4], deta[4], dzeta[4];
+    vis_vars(g, b, u, L[0], L[1], L[2], pL);
+    vis_vars(g, b, u, R[0], R[1], R[2], pR);
+    for (int q = 0; q < 4; ++q) {
+        dxi[q] = pR[q] - pL[q];
+        deta[q] = 0.0;
+        dzeta[q] = 0.0;
+    }
+    for (int t = 0; t < 2; ++t) {
+        int a = t == 0 ? e : f;
+        if (a >= ndir) continue;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            int Lp[3] = {L[0], L[1], L[2]}, Rp[3] = {R[0], R[1], R[2]};
+            Lp[a] += sgn;
+            Rp[a] += sgn;
+            double qa[4], qb[4];
+            vis_vars(g, b, u, Lp[0], Lp[1], Lp[2], qa);
+            vis_vars(g, b, u, Rp[0], Rp[1], Rp[2], qb);
+            for (int q = 0; q < 4; ++q) acc[q] += sgn * (qa[q] + qb[q]);
+        }
+        for (int q = 0; q < 4; ++q) {
+            if (t == 0) deta[q] = 0.25 * acc[q];
+            else dzeta[q] = 0.25 * acc[q];
+        }
+    }
+    /* grad xi_a at the face: (Sbar_a(L) + Sbar_a(R)) / (|Omega_L| + |Omega_R|),
+     * a ghost cell carrying the geometry of the cell it copies */
+    int Lc[3] = {L[0], L[1], L[2]}, Rc[3] = {R[0], R[1], R[2]};
+    const ora_block *bL = metric_cell(g, b, Lc), *bR = metric_cell(g, b, Rc);
+    double vsum = bL->vol[interior(bL, Lc[0], Lc[1], Lc[2])] + bR->vol[interior(bR, Rc[0], Rc[1], Rc[2])];
+    double gx[3][3];   /* gx[m] = grad of the m-th computational coordinate (d, e, f) */
+    int dirs[3] = {d, e, f};
+    for (int m = 0; m < 3; ++m) {
+        if (dirs[m] >= ndir) {
+            gx[m][0] = gx[m][1] = gx[m][2] = 0.0;
+            continue;
+        }
+        double sa[3], sb[3];
+        cell_sbar(bL, dirs[m], Lc[0], Lc[1], Lc[2], sa);
+        cell_sbar(bR, dirs[m], Rc[0], Rc[1], Rc[2], sb);
+        for (int c = 0; c < 3; ++c) gx[m][c] = (sa[c] + sb[c]) / vsum;
+    }
+    double grad[4][3];
+    for (int q = 0; q < 4; ++q)
+        for (int c = 0; c < 3; ++c) grad[q][c] = dxi[q] * gx[0][c] + deta[q] * gx[1][c] + dzeta[q] * gx[2][c];
+    double mu = g->mu;
+    double div = grad[0][0] + grad[1][1] + grad[2][2];
+    double tau[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) tau[a][c] = mu * (grad[a][c] + grad[c][a]) - (a == c ? 2.0 / 3.0 * mu * div : 0.0);
+    double ub[3] = {0.5 * (pL[0] + pR[0]), 0.5 * (pL[1] + pR[1]), 0.5 * (pL[2] + pR[2])};
+    double kappa = mu * g->gamma / ((g->gamma - 1.0) * g->prandtl);
+    double theta[3];
+    for (int c = 0; c < 3; ++c) theta[c] = ub[0] * tau[0][c] + ub[1] * tau[1][c] + ub[2] * tau[2][c] + kappa * grad[3][c];
+    F[0] = 0.0;
+    for (int a = 0; a < 3; ++a) F[1 + a] = tau[a][0] * S[0] + tau[a][1] * S[1] + tau[a][2] * S[2];
+    F[4] = theta[0] * S[0] + theta[1] * S[1] + theta[2] * S[2];
+}
+
 static void block_residual(const ora_grid *g, int bi, double *const *U, double *R, const double *src)
 {
     const ora_block *b = &g->b[bi];
@@ -558,6 +721,11 @@ static void block_residual(const ora_grid *g, int bi, double *const *U, double *
                 for (int m = 0; m < 4; ++m) c[m] = cell(b, i - 2 + m, j, k);
                 for (int a = 0; a < 3; ++a) S[a] = b->Si[a * nfi + fi_index(b, i, j, k)];
                 stencil_flux(g, b, u, c, S, F);
+                if (g->mu > 0.0) {
+                    double Fv[NV];
+                    viscous_flux(g, b, u, 0, i, j, k, S, Fv);
+                    for (int q = 0; q < NV; ++q) F[q] -= Fv[q];
+                }
                 for (int q = 0; q < NV; ++q) Fi[q * nfi + fi_index(b, i, j, k)] = F[q];
             }
     for (int k = 0; k < b->nk; ++k)
@@ -566,6 +734,11 @@ static void block_residual(const ora_grid *g, int bi, double *const *U, double *
                 for (int m = 0; m < 4; ++m) c[m] = cell(b, i, j - 2 + m, k);
                 for (int a = 0; a < 3; ++a) S[a] = b->Sj[a * nfj + fj_index(b, i, j, k)];
                 stencil_flux(g, b, u, c, S, F);
+                if (g->mu > 0.0) {
+                    double Fv[NV];
+                    viscous_flux(g, b, u, 1, i, j, k, S, Fv);
+                    for (int q = 0; q < NV; ++q) F[q] -= Fv[q];
+                }
                 for (int q = 0; q < NV; ++q) Fj[q * nfj + fj_index(b, i, j, k)] = F[q];
             }
     if (!is2d(b))
@@ -575,6 +748,11 @@ static void block_residual(const ora_grid *g, int bi, double *const *U, double *
                     for (int m = 0; m < 4; ++m) c[m] = cell(b, i, j, k - 2 + m);
                     for (int a = 0; a < 3; ++a) S[a] = b->Sk[a * nfk + fk_index(b, i, j, k)];
                     stencil_flux(g, b, u, c, S, F);
+                    if (g->mu > 0.0) {
+                        double Fv[NV];
+                        viscous_flux(g, b, u, 2, i, j, k, S, Fv);
+                        for (int q = 0; q < NV; ++q) F[q] -= Fv[q];
+                    }
                     for (int q = 0; q < NV; ++q) Fk[q * nfk + fk_index(b, i, j, k)] = F[q];
                 }
 
@@ -605,6 +783,16 @@ static void block_residual(const ora_grid *g, int bi, double *const *U, double *
 /* paper states no time-step rule; this spectral-radius bound is the reading */
 /* used.                                                                     */
 /* ------------------------------------------------------------------------ */
+
+/* the viscous part of the spectral radius of direction d (zero for mu = 0):
+ * 4 max(4/3, gamma) mu / (Pr rho) |Sbar_d|^2 / |Omega| (the paper gives no
+ * time-step rule; the factor 4 and the max form are the reading used) */
+static double viscous_radius(const ora_grid *g, double rho, double vol, const double Sb[3])
+{
+    if (!(g->mu > 0.0)) return 0.0;
+    double f = g->gamma > 4.0 / 3.0 ? g->gamma : 4.0 / 3.0;
+    return 4.0 * f * g->mu / (g->prandtl * rho) * (Sb[0] * Sb[0] + Sb[1] * Sb[1] + Sb[2] * Sb[2]) / vol;
+}
 
 static double block_dt_min(const ora_grid *g, int bi, const double *u)
 {
@@ -639,6 +827,7 @@ static double block_dt_min(const ora_grid *g, int bi, const double *u)
                     double uS = W[1] * Sb[0] + W[2] * Sb[1] + W[3] * Sb[2];
                     double mag = sqrt(Sb[0] * Sb[0] + Sb[1] * Sb[1] + Sb[2] * Sb[2]);
                     sum += fabs(uS) + c * mag;
+                    sum += viscous_radius(g, W[0], b->vol[interior(b, i, j, k)], Sb);
                 }
                 double t = b->vol[interior(b, i, j, k)] / sum;
                 if (t < best) best = t;
@@ -773,6 +962,18 @@ void ora_fill_ghosts(const ora_grid *g, double *const *U)
 {
     for (int bi = 0; bi < g->nb; ++bi)
         for (int f = 0; f < (is2d(&g->b[bi]) ? 4 : 6); ++f) fill_face(g, bi, f, U);
+    /* the block-edge ghosts of the viscous face gradients, from the face
+     * ghosts of every block */
+    if (g->mu > 0.0)
+        for (int bi = 0; bi < g->nb; ++bi)
+            for (int f = 0; f < (is2d(&g->b[bi]) ? 4 : 6); ++f) fill_face_range(g, bi, f, U, 1);
+}
+
+/* viscosity (constant mu >= 0; 0 = Euler) and Prandtl number of F_nu */
+void ora_set_viscosity(ora_grid *g, double mu, double prandtl)
+{
+    g->mu = mu;
+    g->prandtl = prandtl;
 }
 
 /* R_h of every block from states whose ghost layers are already filled;
@@ -852,6 +1053,7 @@ static double cell_dt(const ora_grid *g, const ora_block *b, const double *u, in
         double uS = W[1] * Sb[0] + W[2] * Sb[1] + W[3] * Sb[2];
         double mag = sqrt(Sb[0] * Sb[0] + Sb[1] * Sb[1] + Sb[2] * Sb[2]);
         sum += fabs(uS) + c * mag;
+        sum += viscous_radius(g, W[0], b->vol[interior(b, i, j, k)], Sb);
     }
     return cfl * b->vol[interior(b, i, j, k)] / sum;
 }

@@ -58,6 +58,8 @@ class Workload:
     kappa: float = 1.0 / 3.0
     eps: float = 1.0
     fix: float = 0.1
+    mu: float = 0.0                 # dynamic viscosity of F_nu (0: Euler)
+    prandtl: float = 0.72
     note: str = ""
 
     @property

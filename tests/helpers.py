@@ -11,7 +11,8 @@ def oracle_grid(w: wl.Workload, limiter=None, kappa=None, recon_conserved=False,
     lim = wl.LIMITERS[limiter if limiter is not None else w.limiter]
     g = oracle.OracleGrid(w.dims, w.nodes, gamma=w.gamma, limiter=lim,
                           kappa=w.kappa if kappa is None else kappa, eps=w.eps,
-                          recon_conserved=recon_conserved, fix=w.fix if fix is None else fix)
+                          recon_conserved=recon_conserved, fix=w.fix if fix is None else fix,
+                          mu=w.mu, prandtl=w.prandtl)
     for b, faces in enumerate(w.bcs):
         nfaces = 4 if w.dims[b][2] == 1 else 6
         for f in range(nfaces):
@@ -42,7 +43,7 @@ def gpu_grid(w: wl.Workload, limiter=None, precision=0, kappa=None, recon_conser
     lim = wl.LIMITERS[limiter if limiter is not None else w.limiter]
     g = sensei.Grid(w.dims, w.nodes, gamma=w.gamma, limiter=lim, kappa=w.kappa if kappa is None else kappa,
                     eps=w.eps, entropy_fix=w.fix if fix is None else fix, precision=precision,
-                    reconstruct_conserved=recon_conserved)
+                    reconstruct_conserved=recon_conserved, mu=w.mu, prandtl=w.prandtl)
     for b, faces in enumerate(w.bcs):
         nfaces = 4 if w.dims[b][2] == 1 else 6
         for f in range(nfaces):
