@@ -108,6 +108,15 @@ typedef struct {
     double entropy_fix;     /* Harten's fix width delta = entropy_fix * (Roe sound speed); 0 = off */
     int precision;          /* sensei_precision */
     int reconstruct_conserved; /* 0: reconstruct primitive (rho, u, v, w, p); 1: conserved Q */
+    /* Viscous flux F_nu,n of Eq. governing (Stokes's hypothesis; Theta = work
+     * of the viscous stresses + heat conduction).  mu = 0: the Euler
+     * equations.  mu > 0: constant dynamic viscosity, heat conductivity
+     * mu c_p / prandtl; face gradients by central differences in the index
+     * directions and the metric identity grad xi_d = Sbar_d / |Omega| (the
+     * paper fixes neither; these are this library's readings).  FP64
+     * precision only (SENSEI_ERR_UNSUPPORTED otherwise). */
+    double mu;
+    double prandtl;         /* > 0 when mu > 0, e.g. 0.72 */
 } sensei_scheme;
 
 /* Where cell (i, j, k), variable v of a block's state lives: element

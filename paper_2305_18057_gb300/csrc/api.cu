@@ -57,7 +57,8 @@ struct HostBlock {
 // sensei_workspace_size and sensei_create_grid.
 struct Plan {
     std::vector<HostBlock> blocks;
-    std::vector<size_t> off_fn, off_rec32, off_vol, off_ivol, off_sbar, off_sbar32, off_dtv, off_stage;
+    std::vector<size_t> off_fn, off_rec32, off_vol, off_ivol, off_sbar, off_sbar32, off_dtv, off_stage, off_wv,
+        off_rvis;
     size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0;
     size_t bytes = 0;
     long long max_items = 0;   // partial slots (items at the smallest k-chunk)
@@ -84,6 +85,11 @@ sensei_status check_scheme(const sensei_scheme *s)
     if (!(s->entropy_fix >= 0.0)) return fail(SENSEI_ERR_INVALID_ARG, "entropy_fix must be >= 0");
     if (!(s->eps >= 0.0 && s->eps <= 1.0)) return fail(SENSEI_ERR_INVALID_ARG, "eps must lie in [0, 1]");
     if (!(s->kappa >= -1.0 && s->kappa <= 1.0)) return fail(SENSEI_ERR_INVALID_ARG, "kappa must lie in [-1, 1]");
+    if (!(s->mu >= 0.0 && s->mu < INFINITY)) return fail(SENSEI_ERR_INVALID_ARG, "mu must be finite and >= 0");
+    if (s->mu > 0.0 && !(s->prandtl > 0.0 && s->prandtl < INFINITY))
+        return fail(SENSEI_ERR_INVALID_ARG, "prandtl must be finite and > 0 when mu > 0");
+    if (s->mu > 0.0 && s->precision != SENSEI_FP64)
+        return fail(SENSEI_ERR_UNSUPPORTED, "the viscous flux runs in FP64 precision only");
     return SENSEI_OK;
 }
 
@@ -132,6 +138,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     size_t cur = 0;
     P.blocks.resize(nblocks);
     for (auto *v : {&P.off_fn, &P.off_rec32, &P.off_vol, &P.off_ivol, &P.off_sbar, &P.off_sbar32, &P.off_dtv,
+                    &P.off_wv, &P.off_rvis,
                     &P.off_stage})
         v->resize(nblocks);
     const bool f32 = scheme->precision != SENSEI_FP64;
@@ -183,6 +190,10 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         // FP32 spectral metrics (12 arrays) and |Omega| (1) for the FP32 time step
         P.off_sbar32[b] = f32 ? take(cur, 13 * mv * sizeof(float)) : 0;
         P.off_dtv[b] = take(cur, mv * sizeof(double));
+        // viscous: the stage input's (u, v, w, p / rho) and the viscous residual
+        const bool vis = scheme->mu > 0.0;
+        P.off_wv[b] = vis ? take(cur, 4 * (size_t)B.L.sv * sizeof(double)) : 0;
+        P.off_rvis[b] = vis ? take(cur, (size_t)NV * d.ni * d.nj * d.nk * sizeof(double)) : 0;
         // two FP64 stage states, or two FP32 stage states + two FP32 increments
         P.off_stage[b] = take(cur, 2 * (size_t)B.L.elems * sizeof(double));
     }
@@ -335,6 +346,62 @@ sensei_status fill_slot(sensei_grid *g, int slot, double *const *U, cudaStream_t
     return SENSEI_OK;
 }
 
+bool viscous(const sensei_grid *g) { return g->scheme.mu > 0.0; }
+
+// The block-edge ghosts of a slot's states (the face ghosts are in place).
+sensei_status fill_edges(sensei_grid *g, int slot, double *const *U, cudaStream_t s)
+{
+    BCBatch p;
+    memset(&p, 0, sizeof p);
+    p.blocks = g->desc;
+    p.nblocks = (int)g->plan.blocks.size();
+    p.total = g->plan.bc_total;
+    p.slot = slot;
+    p.gamma = g->scheme.gamma;
+    if (U)
+        for (int b = 0; b < p.nblocks; ++b) p.user[b] = U[b];
+    long long max_edges = 0;
+    for (auto &H : g->plan.blocks)
+        max_edges = std::max<long long>(max_edges, 16LL * (H.dev.ni + H.dev.nj + H.dev.nk));
+    CUDA_TRY(launch_edges(p, (int)std::min<long long>(max_edges, 1 << 30), s));
+    g->kernel_launches++;
+    return SENSEI_OK;
+}
+
+// The viscous residual of a slot's states: the block-edge ghosts, then the
+// primitives and R_nu of every block.
+sensei_status viscous_residual(sensei_grid *g, int slot, double *const *U, cudaStream_t s)
+{
+    sensei_status st = fill_edges(g, slot, U, s);
+    if (st != SENSEI_OK) return st;
+    long long max_state = 0, max_cells = 0;
+    for (auto &H : g->plan.blocks) {
+        max_state = std::max<long long>(max_state, H.dev.L.sv);
+        max_cells = std::max<long long>(max_cells, (long long)H.dev.ni * H.dev.nj * H.dev.nk);
+    }
+    const int nb = (int)g->plan.blocks.size();
+    VisBatch v;
+    memset(&v, 0, sizeof v);
+    v.blocks = g->desc;
+    v.nblocks = nb;
+    v.slot = slot;
+    v.gamma = g->scheme.gamma;
+    v.mu = g->scheme.mu;
+    v.kcond = g->scheme.mu * g->scheme.gamma / ((g->scheme.gamma - 1.0) * g->scheme.prandtl);
+    if (U)
+        for (int b = 0; b < nb; ++b) v.user[b] = U[b];
+    CUDA_TRY(launch_viscous(v, max_state, max_cells, s));
+    g->kernel_launches += 2;
+    return SENSEI_OK;
+}
+
+// the viscous time-step factor 4 max(4/3, gamma) mu / Pr (0 without viscosity)
+double viscous_dt_factor(const sensei_grid *g)
+{
+    if (!viscous(g)) return 0.0;
+    return 4.0 * std::max(4.0 / 3.0, g->scheme.gamma) * g->scheme.mu / g->scheme.prandtl;
+}
+
 struct StencilCall {
     int mode;
     int in_slot, out_slot, dprev, dout;
@@ -344,6 +411,7 @@ struct StencilCall {
     const double *dt_slot;
     double dt_scale;
     bool partials;
+    bool vis;
     double *const *user;
     double *const *rout;
     const double *const *src;
@@ -375,6 +443,7 @@ void fill_params(BatchParams<R> &p, const sensei_grid *g, const StencilCall &c)
     p.c2 = p.eps * ((R)1 + p.kappa) * (R)0.25;
     p.half_eps = (R)0.5 * p.eps;
     p.cons = g->scheme.reconstruct_conserved ? 1 : 0;
+    p.vis = c.vis ? 1 : 0;
     p.alpha = c.alpha;
     p.beta = c.beta;
     p.gdt = c.gdt;
@@ -476,7 +545,7 @@ sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, doub
         CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
         CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, local ? 1 : 0,
                            cfl, grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms),
-                           grid->scheme.precision != SENSEI_FP64, s));
+                           grid->scheme.precision != SENSEI_FP64, viscous_dt_factor(grid), s));
         grid->kernel_launches++;
         dt_src = (const double *)grid->dt_bits;
         dt_scale = cfl;
@@ -523,6 +592,13 @@ sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, doub
             c.out_slot = last ? SLOT_USER : SLOT_X0 + stage % 2;
             c.dprev = stage == 0 ? -1 : (stage - 1) % 2;
             c.dout = last ? -1 : stage % 2;
+        }
+        if (viscous(grid)) {
+            // R_nu of the stage input (its face ghosts are in place: filled
+            // for U, pushed by the previous stage otherwise)
+            st = viscous_residual(grid, c.in_slot, U, s);
+            if (st != SENSEI_OK) return st;
+            c.vis = true;
         }
         st = stencil(grid, c, s);
         if (st != SENSEI_OK) return st;
@@ -639,6 +715,8 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
         B.sbar32 = P.off_sbar32[b] ? (const float *)(g->ws + P.off_sbar32[b]) : nullptr;
         B.vol32 = B.sbar32 ? B.sbar32 + 12 * mv : nullptr;
         B.dtv = (double *)(g->ws + P.off_dtv[b]);
+        B.wv = P.off_wv[b] ? (double *)(g->ws + P.off_wv[b]) : nullptr;
+        B.rvis = P.off_rvis[b] ? (double *)(g->ws + P.off_rvis[b]) : nullptr;
         B.st64[0] = (double *)(g->ws + P.off_stage[b]);
         B.st64[1] = B.st64[0] + B.L.elems;
         // FP32 storage reuses the same bytes: X0, X1, D0, D1
@@ -760,6 +838,7 @@ sensei_status sensei_fill_ghosts(sensei_grid *grid, double *const *U, sensei_str
     cudaStream_t s = (cudaStream_t)stream;
     st = sync_descriptors(grid, s);
     if (st == SENSEI_OK) st = fill_slot(grid, SLOT_USER, U, s);
+    if (st == SENSEI_OK && viscous(grid)) st = fill_edges(grid, SLOT_USER, U, s);
     if (st == SENSEI_OK) g_msg[0] = 0;
     return st;
 }
@@ -789,6 +868,11 @@ sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const
     c.user = U;
     c.rout = R;
     c.src = src;
+    if (viscous(grid)) {
+        st = viscous_residual(grid, SLOT_USER, U, s);
+        if (st != SENSEI_OK) return st;
+        c.vis = true;
+    }
     st = stencil(grid, c, s);
     if (st != SENSEI_OK) return st;
     CUDA_TRY(launch_norms_finalize(grid->partials, (int)total_items(grid->plan.blocks), grid->plan.ncells,

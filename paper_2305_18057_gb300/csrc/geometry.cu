@@ -6,6 +6,8 @@
 // extrapolation on the GPU"), two layers per boundary face.
 #include <math.h>
 
+#include <algorithm>
+
 #include "blocks.cuh"
 
 namespace sensei {
@@ -170,6 +172,59 @@ __device__ __forceinline__ float *slot_buffer<float>(const BlockDev &B, double *
     return slot32(B, slot);
 }
 
+// One ghost cell: layer `layer` of face f at tangential position (t1, t2).
+// (t1, t2) may lie one family's ghost layers outside the face (the
+// block-edge ghosts of the viscous face gradients); the rule then reads that
+// family's ghosts, which the face pass has filled, and a wall takes the
+// normal of the nearest boundary face.
+template <typename T>
+__device__ __forceinline__ void fill_one(const BCBatch &p, const BlockDev &B, int b, int f, int layer, int t1, int t2)
+{
+    T *U = slot_buffer<T>(B, p.user[b], p.slot);
+    const int type = B.bc_type[f];
+    int gi, gj, gk, mi, mj, mk, a, bb, c;
+    face_cells(f, B.ni, B.nj, B.nk, t1, t2, layer, 0, gi, gj, gk, a, bb, c);
+    T q[NV];
+    if (type == SENSEI_BC_PERIODIC || type == SENSEI_BC_SLIP_WALL) {
+        // periodic: the opposite face's cell layer-1 inside; wall: the
+        // mirror image of the cell layer-1 inside this face
+        const int src_face = type == SENSEI_BC_PERIODIC ? (f ^ 1) : f;
+        face_cells(src_face, B.ni, B.nj, B.nk, t1, t2, 1, layer - 1, a, bb, c, mi, mj, mk);
+        const long long sc = cell_index(B.L, mi, mj, mk);
+        for (int v = 0; v < NV; ++v) q[v] = U[sc + v * B.L.sv];
+        if (type == SENSEI_BC_SLIP_WALL) {
+            const int n1 = f < 2 ? B.nj : B.ni, n2 = f < 4 ? B.nk : B.nj;
+            double nx, ny, nz;
+            boundary_normal(B, f, min(max(t1, 0), n1 - 1), min(max(t2, 0), n2 - 1), nx, ny, nz);
+            const T tx = (T)nx, ty = (T)ny, tz = (T)nz;
+            const T mn = q[1] * tx + q[2] * ty + q[3] * tz;
+            q[1] -= T(2) * mn * tx;
+            q[2] -= T(2) * mn * ty;
+            q[3] -= T(2) * mn * tz;
+        }
+    } else if (type == SENSEI_BC_EXTRAPOLATE) {
+        const long long sc = cell_index(B.L, a, bb, c);
+        for (int v = 0; v < NV; ++v) q[v] = U[sc + v * B.L.sv];
+    } else if (type == SENSEI_BC_INFLOW) {
+        const double *w = B.bc_prim[f];
+        const double rho = w[0], u = w[1], v = w[2], ww = w[3], pr = w[4];
+        q[0] = (T)rho;
+        q[1] = (T)(rho * u);
+        q[2] = (T)(rho * v);
+        q[3] = (T)(rho * ww);
+        q[4] = (T)(pr / (p.gamma - 1.0) + 0.5 * rho * (u * u + v * v + ww * ww));
+    } else {   // SENSEI_BC_INTERFACE: the neighbour's cell layer-1 inside its face
+        const int nb = B.nbr[f];
+        const BlockDev &N = p.blocks[nb];
+        face_cells(B.nbr_face[f], N.ni, N.nj, N.nk, t1, t2, 1, layer - 1, a, bb, c, mi, mj, mk);
+        const T *NU = slot_buffer<T>(N, p.user[nb], p.slot);
+        const long long sc = cell_index(N.L, mi, mj, mk);
+        for (int v = 0; v < NV; ++v) q[v] = NU[sc + v * N.L.sv];
+    }
+    const long long gc = cell_index(B.L, gi, gj, gk);
+    for (int v = 0; v < NV; ++v) U[gc + v * B.L.sv] = q[v];
+}
+
 template <typename T>
 __global__ void bc_kernel(BCBatch p)
 {
@@ -187,50 +242,53 @@ __global__ void bc_kernel(BCBatch p)
         const int n1 = f < 2 ? B.nj : B.ni;
         const int layer = 1 + (int)(r % 2);
         const long long pos = r / 2;
-        const int t1 = (int)(pos % n1);
-        const int t2 = (int)(pos / n1);
-        T *U = slot_buffer<T>(B, p.user[b], p.slot);
-        const int type = B.bc_type[f];
-        int gi, gj, gk, mi, mj, mk, a, bb, c;
-        face_cells(f, B.ni, B.nj, B.nk, t1, t2, layer, 0, gi, gj, gk, a, bb, c);
-        T q[NV];
-        if (type == SENSEI_BC_PERIODIC || type == SENSEI_BC_SLIP_WALL) {
-            // periodic: the opposite face's cell layer-1 inside; wall: the
-            // mirror image of the cell layer-1 inside this face
-            const int src_face = type == SENSEI_BC_PERIODIC ? (f ^ 1) : f;
-            face_cells(src_face, B.ni, B.nj, B.nk, t1, t2, 1, layer - 1, a, bb, c, mi, mj, mk);
-            const long long sc = cell_index(B.L, mi, mj, mk);
-            for (int v = 0; v < NV; ++v) q[v] = U[sc + v * B.L.sv];
-            if (type == SENSEI_BC_SLIP_WALL) {
-                double nx, ny, nz;
-                boundary_normal(B, f, t1, t2, nx, ny, nz);
-                const T tx = (T)nx, ty = (T)ny, tz = (T)nz;
-                const T mn = q[1] * tx + q[2] * ty + q[3] * tz;
-                q[1] -= T(2) * mn * tx;
-                q[2] -= T(2) * mn * ty;
-                q[3] -= T(2) * mn * tz;
+        fill_one<T>(p, B, b, f, layer, (int)(pos % n1), (int)(pos / n1));
+    }
+}
+
+// q = 0..3 -> -2, -1, n, n + 1: the ghost positions of one index
+__device__ __forceinline__ int ghost_pos(int q, int n) { return q < 2 ? q - 2 : n + q - 2; }
+
+// The block-edge ghosts (two indices outside the block) read by the viscous
+// face gradients, after every face's own ghosts: i-faces fill those at j- or
+// k-ghost positions, j-faces those at k-ghost positions (the rule of the
+// lower face family).  One grid row (blockIdx.y) per block.
+template <typename T>
+__global__ void edge_kernel(BCBatch p)
+{
+    const int b = blockIdx.y;
+    const BlockDev &B = p.blocks[b];
+    const bool two_d = B.nk == 1;
+    const long long pi = two_d ? 4 : 4LL * B.nk + 4LL * B.nj;   // positions per i-face
+    const long long pj = two_d ? 0 : 4LL * B.ni;                // positions per j-face
+    const long long total = 2 * 2 * (pi + pj);                   // two faces per family, two layers
+    for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < total;
+         u += (long long)gridDim.x * blockDim.x) {
+        const int layer = 1 + (int)(u & 1);
+        long long r = u >> 1;
+        int f, t1, t2;
+        if (r < 2 * pi) {
+            f = (int)(r / pi);
+            long long q = r - f * pi;
+            if (two_d) {
+                t1 = ghost_pos((int)q, B.nj);
+                t2 = 0;
+            } else if (q < 4LL * B.nk) {
+                t1 = ghost_pos((int)(q % 4), B.nj);
+                t2 = (int)(q / 4);
+            } else {
+                q -= 4LL * B.nk;
+                t1 = (int)(q / 4);
+                t2 = ghost_pos((int)(q % 4), B.nk);
             }
-        } else if (type == SENSEI_BC_EXTRAPOLATE) {
-            const long long sc = cell_index(B.L, a, bb, c);
-            for (int v = 0; v < NV; ++v) q[v] = U[sc + v * B.L.sv];
-        } else if (type == SENSEI_BC_INFLOW) {
-            const double *w = B.bc_prim[f];
-            const double rho = w[0], u = w[1], v = w[2], ww = w[3], pr = w[4];
-            q[0] = (T)rho;
-            q[1] = (T)(rho * u);
-            q[2] = (T)(rho * v);
-            q[3] = (T)(rho * ww);
-            q[4] = (T)(pr / (p.gamma - 1.0) + 0.5 * rho * (u * u + v * v + ww * ww));
-        } else {   // SENSEI_BC_INTERFACE: the neighbour's cell layer-1 inside its face
-            const int nb = B.nbr[f];
-            const BlockDev &N = p.blocks[nb];
-            face_cells(B.nbr_face[f], N.ni, N.nj, N.nk, t1, t2, 1, layer - 1, a, bb, c, mi, mj, mk);
-            const T *NU = slot_buffer<T>(N, p.user[nb], p.slot);
-            const long long sc = cell_index(N.L, mi, mj, mk);
-            for (int v = 0; v < NV; ++v) q[v] = NU[sc + v * N.L.sv];
+        } else {
+            r -= 2 * pi;
+            f = 2 + (int)(r / pj);
+            const long long q = r - (f - 2) * pj;
+            t1 = (int)(q / 4);
+            t2 = ghost_pos((int)(q % 4), B.nk);
         }
-        const long long gc = cell_index(B.L, gi, gj, gk);
-        for (int v = 0; v < NV; ++v) U[gc + v * B.L.sv] = q[v];
+        fill_one<T>(p, B, b, f, layer, t1, t2);
     }
 }
 
@@ -253,6 +311,16 @@ cudaError_t launch_pack_records(const BlockDev &B, cudaStream_t s)
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     pack_records_kernel<<<(unsigned)blocks, 256, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edges(const BCBatch &p, int max_units, cudaStream_t s)
+{
+    const dim3 grid((unsigned)std::max(1, std::min((max_units + 255) / 256, 64)), (unsigned)p.nblocks);
+    if (p.slot >= SLOT_X0)
+        edge_kernel<float><<<grid, 256, 0, s>>>(p);
+    else
+        edge_kernel<double><<<grid, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

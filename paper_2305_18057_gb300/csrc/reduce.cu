@@ -77,7 +77,7 @@ template <typename R>
 __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, int nblocks, long long nitems,
                                                       const __grid_constant__ DtUser user, double gamma,
                                                       int local, double cfl, unsigned long long *dt_bits,
-                                                      unsigned *err)
+                                                      unsigned *err, double vfac)
 {
     using M = DtMath<R>;
     const int t = threadIdx.x;
@@ -114,10 +114,16 @@ __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, in
             const R a = a2 * M::rsqrt(a2);
             const long long m = k * B.ml.mplane + j * B.ml.mpitch + i;
             R sum = R(0);
+            // viscous bound per direction: vfac / rho |Sbar_d|^2 / |Omega| (FP64 only)
+            const double vr = vfac > 0.0 ? vfac * (double)ir * B.ivol[m] : 0.0;
             for (int d = 0; d < ndir; ++d) {
                 const long long q = (long long)(d * 4) * mv + m;
                 const R un = u * M::sb(B, q) + v * M::sb(B, mv + q) + w * M::sb(B, 2 * mv + q);
                 sum += fabs(un) + a * M::sb(B, 3 * mv + q);
+                if (vfac > 0.0) {
+                    const double s3 = (double)M::sb(B, 3 * mv + q);
+                    sum += (R)(vr * (s3 * s3));
+                }
             }
             const R isum = M::rcp(sum);
             if (local) B.dtv[m] = cfl * (double)isum;
@@ -167,14 +173,15 @@ __global__ void norms_finalize_kernel(const double *__restrict__ partials, int n
 
 cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
                       int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, bool fp32,
-                      cudaStream_t s)
+                      double vfac, cudaStream_t s)
 {
     DtUser u;
     for (int b = 0; b < nblocks; ++b) u.u[b] = user[b];
     if (fp32)
-        dt_kernel<float><<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, local, cfl, dt_bits, err);
+        dt_kernel<float><<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, local, cfl, dt_bits, err, 0.0);
     else
-        dt_kernel<double><<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, local, cfl, dt_bits, err);
+        dt_kernel<double><<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, local, cfl, dt_bits, err,
+                                                    vfac);
     return cudaGetLastError();
 }
 

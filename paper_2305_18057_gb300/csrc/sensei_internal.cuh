@@ -83,6 +83,8 @@ struct BlockDev {
     const double *sbar;     // spectral metrics: 12 arrays of mvolume, index (direction*4 + q)
     const float *sbar32, *vol32;   // their FP32 copies and |Omega| in FP32 (null in FP64 mode)
     double *dtv;            // local time stepping: dt_c / |Omega| per cell (mvolume)
+    double *wv;             // viscous: (u, v, w, p / rho) of the stage input, state layout, 4 variables
+    double *rvis;           // viscous: R_nu = sum over the faces of F_nu . S_out, dense interior [5][nk][nj][ni]
     double *st64[2];        // FP64 stage states
     float *xs[2], *ds[2];   // FP32 stage states and increments
     int tiles_i, tiles_j, kchunk, nchunks;
@@ -124,6 +126,7 @@ struct BatchParams {
     R gamma, kappa, eps, fix;
     R gm1, kg, c1, c2, half_eps;   // gamma - 1, gamma / (gamma - 1), eps (1 -+ kappa) / 4, eps / 2 in R
     int cons;
+    int vis;                // subtract the viscous residual B.rvis
     double alpha, beta, gdt;
     const double *dt_slot;  // dt = dt_scale * *dt_slot
     double dt_scale;
@@ -132,6 +135,16 @@ struct BatchParams {
     double *user[MAX_BLOCKS];        // the caller's U, per block
     double *rout[MAX_BLOCKS];        // MODE_RESIDUAL: R[5][nk][nj][ni]
     const double *src[MAX_BLOCKS];   // MODE_RESIDUAL: |Omega| S_h (or null)
+};
+
+// The viscous residual of every block's stage input (FP64 slots).
+struct VisBatch {
+    const BlockDev *blocks;
+    int nblocks;
+    int slot;               // SLOT_USER or SLOT_ST*
+    double gamma, mu;
+    double kcond;           // mu gamma / ((gamma - 1) Pr)
+    double *user[MAX_BLOCKS];
 };
 
 // Ghost fill of every boundary face of every block of one buffer slot.
@@ -150,6 +163,9 @@ struct BCBatch {
 cudaError_t launch_metrics(int ni, int nj, int nk, const double *X, const MetricsOut &mo,
                            const MetricLayout &ml, cudaStream_t s);
 cudaError_t launch_bc(const BCBatch &p, cudaStream_t s);
+// the block-edge ghosts of every block of one slot (after launch_bc of the
+// slot); max_units: the largest per-block count, 16 (ni + nj + nk)
+cudaError_t launch_edges(const BCBatch &p, int max_units, cudaStream_t s);
 // pack block B's FP64 face metrics and 1/|Omega| into its FP32 records B.rec32
 cudaError_t launch_pack_records(const BlockDev &B, cudaStream_t s);
 // FP64 arithmetic on an FP64 state
@@ -165,10 +181,15 @@ int stencil_ctas_per_sm_f32(int precision_kind, int limiter, bool two_d);
 int stencil_ctas_per_sm_f32s(int limiter, bool two_d);
 // min over cells of |Omega| / sum_d (|u.Sbar_d| + c |Sbar_d|) into dt_bits; with local set,
 // also dtv = cfl / sum_d (...) = dt_c / |Omega| per cell
-// fp32: FP32 arithmetic on the FP32 metric copies (the mixed-precision modes)
+// fp32: FP32 arithmetic on the FP32 metric copies (the mixed-precision modes);
+// vfac = 4 max(4/3, gamma) mu / Pr adds the viscous bound vfac |Sbar_d|^2 / (rho |Omega|)
 cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
                       int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, bool fp32,
-                      cudaStream_t s);
+                      double vfac, cudaStream_t s);
+// the viscous residual B.rvis of the slot's states (after the slot's face
+// and edge ghosts); max_state, max_cells: the largest block's state entries
+// per variable and interior cells
+cudaError_t launch_viscous(const VisBatch &p, long long max_state, long long max_cells, cudaStream_t s);
 cudaError_t launch_set_scalar(double *slot, double v, cudaStream_t s);
 cudaError_t launch_scale_copy(double *dst, const double *src, double scale, cudaStream_t s);
 // Record the thread-local message returned by sensei_last_error (api.cu).

@@ -691,6 +691,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         double r = cvt<double, R>(rres[v]);
+                        if (p.vis) r -= B.rvis[v * nint + rc];   // R = sum (F_i - F_nu) . S
                         if (p.mode == MODE_RESIDUAL && p.src[b]) r -= p.src[b][v * nint + rc];
                         const double uin = cvt<double, TS>(in[cell + v * L.sv]);
                         if (p.mode == MODE_ACCUM) {

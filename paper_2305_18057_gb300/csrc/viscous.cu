@@ -1,0 +1,211 @@
+// viscous.cu -- the viscous flux F_nu,n of Eq. governing on the device.
+//
+// tau_ij from Stokes's hypothesis, Theta_i = u_j tau_ij + k dT/dx_i with a
+// constant mu and k dT = mu gamma / ((gamma - 1) Pr) d(p / rho) (the paper
+// gives neither the viscosity law nor the face-gradient discretisation;
+// these are the readings used).  The gradients of (u, v, w, p / rho) at a
+// face between cells L and R (direction d, tangential directions e, f) are
+//   d/dxi   = phi_R - phi_L,
+//   d/deta  = [(phi_L + phi_R)(+e) - (phi_L + phi_R)(-e)] / 4, likewise zeta,
+//   grad = sum_a d/dxi_a * (Sbar_a(L) + Sbar_a(R)) / (|Omega_L| + |Omega_R|),
+// Sbar_a the mean of a cell's two a-face vectors (the metric identity
+// grad xi_a = Sbar_a / |Omega|), a ghost cell carrying the geometry of the
+// cell it copies.  The tangential differences read the block-edge ghosts.
+//
+// Two kernels per stage: the primitives (u, v, w, p / rho) of every ghosted
+// cell, then per interior cell the sum over its faces of F_nu . S_out
+// (R_nu), which the stencil kernel subtracts from the inviscid residual.
+// Each face's flux is evaluated by both of its cells from the same operands
+// in the same order, so the pair cancels exactly in conservation sums.
+#include <math.h>
+
+#include <algorithm>
+
+#include "blocks.cuh"
+
+namespace sensei {
+namespace {
+
+__device__ __forceinline__ double rcp2(double d)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    for (int n = 0; n < 2; ++n) r = fma(r, fma(-d, r, 1.0), r);
+    return r;
+}
+
+// (u, v, w, p / rho) of every entry of each block's ghosted state array
+__global__ void vis_prims_kernel(VisBatch p)
+{
+    const int b = blockIdx.y;
+    const BlockDev &B = p.blocks[b];
+    const double *U = slot64(B, p.user[b], p.slot);
+    const long long n = B.L.sv;
+    const double gm1 = p.gamma - 1.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const double rho = U[e], mx = U[n + e], my = U[2 * n + e], mz = U[3 * n + e], E = U[4 * n + e];
+        const double ir = rcp2(rho);
+        const double u = mx * ir, v = my * ir, w = mz * ir;
+        const double pr = gm1 * (E - 0.5 * (mx * u + my * v + mz * w));
+        B.wv[e] = u;
+        B.wv[n + e] = v;
+        B.wv[2 * n + e] = w;
+        B.wv[3 * n + e] = pr * ir;
+    }
+}
+
+// The cell whose geometry cell c (of a face's two cells) carries: itself
+// inside the block; behind a periodic face the opposite side's cell; behind
+// an interface the neighbour block's cell; behind a physical boundary the
+// boundary cell it mirrors.
+__device__ __forceinline__ const BlockDev *metric_cell(const BlockDev *blocks, const BlockDev *B, int c[3])
+{
+    const int n[3] = {B->ni, B->nj, B->nk};
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] >= 0 && c[a] < n[a]) continue;
+        const int hi = c[a] >= n[a];
+        const int f = 2 * a + hi;
+        const int layer = hi ? c[a] - n[a] + 1 : -c[a];
+        const int type = B->bc_type[f];
+        if (type == SENSEI_BC_PERIODIC) {
+            c[a] = hi ? c[a] - n[a] : c[a] + n[a];
+        } else if (type == SENSEI_BC_INTERFACE) {
+            const BlockDev *N = &blocks[B->nbr[f]];
+            const int m[3] = {N->ni, N->nj, N->nk};
+            c[a] = (B->nbr_face[f] & 1) ? m[a] - layer : layer - 1;
+            return N;
+        } else {
+            c[a] = min(max(c[a], 0), n[a] - 1);
+        }
+    }
+    return B;
+}
+
+__device__ __forceinline__ long long mindex(const BlockDev *B, int i, int j, int k)
+{
+    return (long long)k * B->ml.mplane + (long long)j * B->ml.mpitch + i;
+}
+
+// F_nu . S through the d-face between L = (i, j, k) - e_d and R = (i, j, k)
+__device__ void face_flux_nu(const VisBatch &p, const BlockDev &B, int d, int i, int j, int k, double F[NV])
+{
+    const int ndir = B.nk == 1 ? 2 : 3;
+    const int L[3] = {i - (d == 0), j - (d == 1), k - (d == 2)};
+    const int Rr[3] = {i, j, k};
+    const int e = d == 0 ? 1 : 0;
+    const int f = d == 2 ? 1 : 2;
+    const long long sv = B.L.sv;
+    const double *wv = B.wv;
+    const long long cL = cell_index(B.L, L[0], L[1], L[2]), cR = cell_index(B.L, i, j, k);
+    double pL[4], pR[4], dxi[4], deta[4], dzeta[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        pL[q] = wv[q * sv + cL];
+        pR[q] = wv[q * sv + cR];
+        dxi[q] = pR[q] - pL[q];
+        deta[q] = 0.0;
+        dzeta[q] = 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int a = t == 0 ? e : f;
+        if (a >= ndir) continue;
+        const int da = a == 0, db = a == 1, dc = a == 2;
+        const long long off = (long long)dc * B.L.sk + (long long)db * B.L.sj + da;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // (-1) then (+1), the order of the sum in the reading above
+            double acc = -(wv[q * sv + cL - off] + wv[q * sv + cR - off]);
+            acc += wv[q * sv + cL + off] + wv[q * sv + cR + off];
+            if (t == 0)
+                deta[q] = 0.25 * acc;
+            else
+                dzeta[q] = 0.25 * acc;
+        }
+    }
+    int Lc[3] = {L[0], L[1], L[2]}, Rc[3] = {Rr[0], Rr[1], Rr[2]};
+    const BlockDev *bL = metric_cell(p.blocks, &B, Lc);
+    const BlockDev *bR = metric_cell(p.blocks, &B, Rc);
+    const long long mL = mindex(bL, Lc[0], Lc[1], Lc[2]), mR = mindex(bR, Rc[0], Rc[1], Rc[2]);
+    const double ivs = 1.0 / (bL->vol[mL] + bR->vol[mR]);
+    const int dirs[3] = {d, e, f};
+    double gx[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        if (dirs[m] >= ndir) {
+            gx[m][0] = gx[m][1] = gx[m][2] = 0.0;
+            continue;
+        }
+        const double *sa = bL->sbar + (long long)(dirs[m] * 4) * bL->ml.mvolume + mL;
+        const double *sb = bR->sbar + (long long)(dirs[m] * 4) * bR->ml.mvolume + mR;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gx[m][c] = (sa[c * bL->ml.mvolume] + sb[c * bR->ml.mvolume]) * ivs;
+    }
+    double grad[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) grad[q][c] = dxi[q] * gx[0][c] + deta[q] * gx[1][c] + dzeta[q] * gx[2][c];
+    const double mu = p.mu;
+    const double div = grad[0][0] + grad[1][1] + grad[2][2];
+    double tau[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            tau[a][c] = mu * (grad[a][c] + grad[c][a]) - (a == c ? 2.0 / 3.0 * mu * div : 0.0);
+    const double ub[3] = {0.5 * (pL[0] + pR[0]), 0.5 * (pL[1] + pR[1]), 0.5 * (pL[2] + pR[2])};
+    double theta[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        theta[c] = ub[0] * tau[0][c] + ub[1] * tau[1][c] + ub[2] * tau[2][c] + p.kcond * grad[3][c];
+    // the face's area vector, unit normal x area
+    const long long mf = mindex(&B, i, j, k);
+    const double *fn = B.fn + (long long)(d * 4) * B.ml.mvolume + mf;
+    const double A = fn[3 * B.ml.mvolume];
+    const double S[3] = {fn[0] * A, fn[B.ml.mvolume] * A, fn[2 * B.ml.mvolume] * A};
+    F[0] = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[1 + a] = tau[a][0] * S[0] + tau[a][1] * S[1] + tau[a][2] * S[2];
+    F[4] = theta[0] * S[0] + theta[1] * S[1] + theta[2] * S[2];
+}
+
+// R_nu = sum over a cell's faces of F_nu . S_out, dense interior layout
+__global__ void __launch_bounds__(256) vis_residual_kernel(VisBatch p)
+{
+    const int b = blockIdx.y;
+    const BlockDev &B = p.blocks[b];
+    const long long nint = (long long)B.ni * B.nj * B.nk;
+    const int ndir = B.nk == 1 ? 2 : 3;
+    for (long long rc = blockIdx.x * (long long)blockDim.x + threadIdx.x; rc < nint;
+         rc += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(rc % B.ni);
+        const int j = (int)((rc / B.ni) % B.nj);
+        const int k = (int)(rc / ((long long)B.ni * B.nj));
+        double acc[NV] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int d = 0; d < ndir; ++d) {
+            double Flo[NV], Fhi[NV];
+            face_flux_nu(p, B, d, i, j, k, Flo);
+            face_flux_nu(p, B, d, i + (d == 0), j + (d == 1), k + (d == 2), Fhi);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) acc[q] += Fhi[q] - Flo[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) B.rvis[q * nint + rc] = acc[q];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_viscous(const VisBatch &p, long long max_state, long long max_cells, cudaStream_t s)
+{
+    const unsigned gx1 = (unsigned)std::max<long long>(1, std::min<long long>((max_state + 255) / 256, 1024));
+    vis_prims_kernel<<<dim3(gx1, (unsigned)p.nblocks), 256, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned gx2 = (unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 1024));
+    vis_residual_kernel<<<dim3(gx2, (unsigned)p.nblocks), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace sensei

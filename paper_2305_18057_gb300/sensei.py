@@ -39,7 +39,8 @@ class BlockDesc(C.Structure):
 
 class Scheme(C.Structure):
     _fields_ = [("gamma", C.c_double), ("limiter", C.c_int), ("kappa", C.c_double), ("eps", C.c_double),
-                ("entropy_fix", C.c_double), ("precision", C.c_int), ("reconstruct_conserved", C.c_int)]
+                ("entropy_fix", C.c_double), ("precision", C.c_int), ("reconstruct_conserved", C.c_int),
+                ("mu", C.c_double), ("prandtl", C.c_double)]
 
 
 class Layout(C.Structure):
@@ -246,7 +247,8 @@ class Grid:
         self.blocks = [tuple(int(v) for v in d) for d in blocks]
         self.scheme = Scheme(scheme.get("gamma", 1.4), scheme.get("limiter", LIM_VANLEER),
                              scheme.get("kappa", 1.0 / 3.0), scheme.get("eps", 1.0), scheme.get("entropy_fix", 0.1),
-                             scheme.get("precision", FP64), int(scheme.get("reconstruct_conserved", 0)))
+                             scheme.get("precision", FP64), int(scheme.get("reconstruct_conserved", 0)),
+                             scheme.get("mu", 0.0), scheme.get("prandtl", 0.72))
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ws_bytes = sensei_workspace_size(self.blocks, self.scheme)

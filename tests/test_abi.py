@@ -62,12 +62,21 @@ def test_invalid_arguments_rejected_on_host(sensei):
         ([(4, 4, 4)], _scheme(sensei, precision=9)),
         ([(4, 4, 4)], _scheme(sensei, eps=2.0)),
         ([(4, 4, 4)], _scheme(sensei, entropy_fix=-1.0)),
+        ([(4, 4, 4)], _scheme(sensei, mu=-1.0, prandtl=0.72)),
+        ([(4, 4, 4)], _scheme(sensei, mu=1e-3, prandtl=0.0)),
     ]
     for blocks, sch in bad:
         with pytest.raises(sensei.SenseiError) as e:
             sensei.sensei_workspace_size(blocks, sch)
         assert e.value.status == sensei.ERR_INVALID_ARG
         assert sensei.sensei_last_error() != ""
+    # the viscous flux is FP64 only
+    with pytest.raises(sensei.SenseiError) as e:
+        sensei.sensei_workspace_size([(4, 4, 4)], _scheme(sensei, mu=1e-3, prandtl=0.72, precision=sensei.FP32_FLUX))
+    assert e.value.status == sensei.ERR_UNSUPPORTED
+    # its workspace adds the primitives and the viscous residual
+    assert sensei.sensei_workspace_size([(32, 16, 8)], _scheme(sensei, mu=1e-3, prandtl=0.72)) > \
+        sensei.sensei_workspace_size([(32, 16, 8)], _scheme(sensei))
     # the FP32-storage form fits its FP32 stage states in the FP64 stage buffers
     assert sensei.sensei_workspace_size([(32, 16, 8)], _scheme(sensei, precision=sensei.FP32_STORE)) > 0
     L = sensei.load()
