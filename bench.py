@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -180,7 +182,7 @@ def gpu_setup(w, precision, tune=True):
     import torch
     from paper_2305_18057_gb300 import sensei, workloads as wl
     g = sensei.Grid(w.dims, w.nodes, gamma=w.gamma, limiter=wl.LIMITERS[w.limiter], kappa=w.kappa, eps=w.eps,
-                    entropy_fix=w.fix, precision=precision)
+                    entropy_fix=w.fix, precision=precision, mu=w.mu, prandtl=w.prandtl)
     for b, faces in enumerate(w.bcs):
         for f in range(4 if w.dims[b][2] == 1 else 6):
             bc = faces[f]
@@ -479,6 +481,25 @@ def main():
                              "kernel_ms_per_launch": stv, "alg_bytes_per_launch": bv, "peak_source": peak_src}}
             del gv, Uv
         del g64, U64
+        # the Navier-Stokes form (NEXT row f2) in FP64 on the same grid and
+        # state, with the viscosity of a Reynolds number of 1000 on the mean
+        # speed and density and a unit length
+        import dataclasses
+        speed = float(np.sqrt(sum(float(np.mean(w.U0[0][a] / w.U0[0][0])) ** 2 for a in (1, 2, 3))))
+        rho_m = float(np.mean(w.U0[0][0]))
+        mu = rho_m * speed / 1000.0
+        wv = dataclasses.replace(w, mu=mu)
+        gv, Uv, sched_v = gpu_setup(wv, sensei.FP64)
+        for _ in range(args.warmup):
+            gv.rk_step(Uv, rk, cfl=w.cfl)
+        msv, profv = time_steps(gv, Uv, args.steps, rk, w.cfl, profile=True)
+        line["variants"]["fp64_viscous"] = {
+            "value": cells * stages * args.steps / (msv / 1e3), "unit": UNIT, "ms_per_step": msv / args.steps,
+            "mu": mu, "prandtl": wv.prandtl, "reynolds": 1000,
+            "stencil_ms_per_step": profv[0] / args.steps,
+            "viscous_and_ghost_ms_per_step": msv / args.steps - profv[0] / args.steps,
+            "note": "FP64 Navier-Stokes: edge ghosts + primitives + viscous residual kernels before each stage"}
+        del gv, Uv
 
     # the performance model of Sec. 6 on this GPU: the 2D ramp at three N_l
     # with N_w = 1024, each cut into P = 1, 4, 16, 64 i-blocks (the model's

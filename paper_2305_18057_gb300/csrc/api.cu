@@ -58,7 +58,7 @@ struct HostBlock {
 struct Plan {
     std::vector<HostBlock> blocks;
     std::vector<size_t> off_fn, off_rec32, off_vol, off_ivol, off_sbar, off_sbar32, off_dtv, off_stage, off_wv,
-        off_rvis;
+        off_rvis, off_fvis, off_gvis;
     size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0;
     size_t bytes = 0;
     long long max_items = 0;   // partial slots (items at the smallest k-chunk)
@@ -138,7 +138,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     size_t cur = 0;
     P.blocks.resize(nblocks);
     for (auto *v : {&P.off_fn, &P.off_rec32, &P.off_vol, &P.off_ivol, &P.off_sbar, &P.off_sbar32, &P.off_dtv,
-                    &P.off_wv, &P.off_rvis,
+                    &P.off_wv, &P.off_rvis, &P.off_fvis, &P.off_gvis,
                     &P.off_stage})
         v->resize(nblocks);
     const bool f32 = scheme->precision != SENSEI_FP64;
@@ -194,6 +194,8 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         const bool vis = scheme->mu > 0.0;
         P.off_wv[b] = vis ? take(cur, 4 * (size_t)B.L.sv * sizeof(double)) : 0;
         P.off_rvis[b] = vis ? take(cur, (size_t)NV * d.ni * d.nj * d.nk * sizeof(double)) : 0;
+        P.off_fvis[b] = vis ? take(cur, 3 * (size_t)NV * mv * sizeof(double)) : 0;
+        P.off_gvis[b] = vis ? take(cur, 27 * mv * sizeof(double)) : 0;
         // two FP64 stage states, or two FP32 stage states + two FP32 increments
         P.off_stage[b] = take(cur, 2 * (size_t)B.L.elems * sizeof(double));
     }
@@ -325,6 +327,13 @@ sensei_status sync_descriptors(sensei_grid *g, cudaStream_t s)
     std::vector<BlockDev> tab(g->plan.blocks.size());
     for (size_t b = 0; b < tab.size(); ++b) tab[b] = g->plan.blocks[b].dev;
     CUDA_TRY(cudaMemcpyAsync(g->desc, tab.data(), tab.size() * sizeof(BlockDev), cudaMemcpyHostToDevice, s));
+    if (g->scheme.mu > 0.0) {
+        // the viscous face metrics follow the boundary rules (the geometry a
+        // ghost cell carries)
+        long long max_faces = 0;
+        for (auto &H : g->plan.blocks) max_faces = std::max<long long>(max_faces, H.dev.ml.mvolume);
+        CUDA_TRY(launch_vis_metrics(g->desc, (int)tab.size(), max_faces, s));
+    }
     CUDA_TRY(cudaStreamSynchronize(s));
     g->dirty = false;
     return SENSEI_OK;
@@ -374,9 +383,10 @@ sensei_status viscous_residual(sensei_grid *g, int slot, double *const *U, cudaS
 {
     sensei_status st = fill_edges(g, slot, U, s);
     if (st != SENSEI_OK) return st;
-    long long max_state = 0, max_cells = 0;
+    long long max_state = 0, max_faces = 0, max_cells = 0;
     for (auto &H : g->plan.blocks) {
         max_state = std::max<long long>(max_state, H.dev.L.sv);
+        max_faces = std::max<long long>(max_faces, H.dev.ml.mvolume);
         max_cells = std::max<long long>(max_cells, (long long)H.dev.ni * H.dev.nj * H.dev.nk);
     }
     const int nb = (int)g->plan.blocks.size();
@@ -390,8 +400,8 @@ sensei_status viscous_residual(sensei_grid *g, int slot, double *const *U, cudaS
     v.kcond = g->scheme.mu * g->scheme.gamma / ((g->scheme.gamma - 1.0) * g->scheme.prandtl);
     if (U)
         for (int b = 0; b < nb; ++b) v.user[b] = U[b];
-    CUDA_TRY(launch_viscous(v, max_state, max_cells, s));
-    g->kernel_launches += 2;
+    CUDA_TRY(launch_viscous(v, max_state, max_faces, max_cells, s));
+    g->kernel_launches += 3;
     return SENSEI_OK;
 }
 
@@ -717,6 +727,8 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
         B.dtv = (double *)(g->ws + P.off_dtv[b]);
         B.wv = P.off_wv[b] ? (double *)(g->ws + P.off_wv[b]) : nullptr;
         B.rvis = P.off_rvis[b] ? (double *)(g->ws + P.off_rvis[b]) : nullptr;
+        B.fvis = P.off_fvis[b] ? (double *)(g->ws + P.off_fvis[b]) : nullptr;
+        B.gvis = P.off_gvis[b] ? (double *)(g->ws + P.off_gvis[b]) : nullptr;
         B.st64[0] = (double *)(g->ws + P.off_stage[b]);
         B.st64[1] = B.st64[0] + B.L.elems;
         // FP32 storage reuses the same bytes: X0, X1, D0, D1

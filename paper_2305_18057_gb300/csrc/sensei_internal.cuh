@@ -85,6 +85,8 @@ struct BlockDev {
     double *dtv;            // local time stepping: dt_c / |Omega| per cell (mvolume)
     double *wv;             // viscous: (u, v, w, p / rho) of the stage input, state layout, 4 variables
     double *rvis;           // viscous: R_nu = sum over the faces of F_nu . S_out, dense interior [5][nk][nj][ni]
+    double *fvis;           // viscous: F_nu . S of every face, [family * 5 + q][mvolume]
+    double *gvis;           // viscous: grad xi_a at every face, [family * 9 + a * 3 + c][mvolume]
     double *st64[2];        // FP64 stage states
     float *xs[2], *ds[2];   // FP32 stage states and increments
     int tiles_i, tiles_j, kchunk, nchunks;
@@ -186,10 +188,14 @@ int stencil_ctas_per_sm_f32s(int limiter, bool two_d);
 cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
                       int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, bool fp32,
                       double vfac, cudaStream_t s);
+// the face gradient metrics B.gvis of every block (after the descriptors
+// with the boundary rules are on the device); max_faces: the largest mvolume
+cudaError_t launch_vis_metrics(const BlockDev *blocks, int nblocks, long long max_faces, cudaStream_t s);
 // the viscous residual B.rvis of the slot's states (after the slot's face
-// and edge ghosts); max_state, max_cells: the largest block's state entries
-// per variable and interior cells
-cudaError_t launch_viscous(const VisBatch &p, long long max_state, long long max_cells, cudaStream_t s);
+// and edge ghosts); max_state, max_faces, max_cells: the largest block's
+// state entries per variable, mvolume and interior cells
+cudaError_t launch_viscous(const VisBatch &p, long long max_state, long long max_faces, long long max_cells,
+                           cudaStream_t s);
 cudaError_t launch_set_scalar(double *slot, double v, cudaStream_t s);
 cudaError_t launch_scale_copy(double *dst, const double *src, double scale, cudaStream_t s);
 // Record the thread-local message returned by sensei_last_error (api.cu).

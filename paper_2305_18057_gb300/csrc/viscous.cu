@@ -12,11 +12,12 @@
 // grad xi_a = Sbar_a / |Omega|), a ghost cell carrying the geometry of the
 // cell it copies.  The tangential differences read the block-edge ghosts.
 //
-// Two kernels per stage: the primitives (u, v, w, p / rho) of every ghosted
-// cell, then per interior cell the sum over its faces of F_nu . S_out
-// (R_nu), which the stencil kernel subtracts from the inviscid residual.
-// Each face's flux is evaluated by both of its cells from the same operands
-// in the same order, so the pair cancels exactly in conservation sums.
+// Per grid (and whenever the boundary rules change) the face gradient
+// metrics grad xi_a of every face.  Per stage three kernels: the primitives
+// (u, v, w, p / rho) of every ghosted cell; F_nu . S of every face, once;
+// per interior cell the sum over its faces (R_nu), which the stencil kernel
+// subtracts from the inviscid residual.  A face's one value enters both of
+// its cells, so the pair cancels exactly in conservation sums.
 #include <math.h>
 
 #include <algorithm>
@@ -86,109 +87,140 @@ __device__ __forceinline__ long long mindex(const BlockDev *B, int i, int j, int
     return (long long)k * B->ml.mplane + (long long)j * B->ml.mpitch + i;
 }
 
-// F_nu . S through the d-face between L = (i, j, k) - e_d and R = (i, j, k)
-__device__ void face_flux_nu(const VisBatch &p, const BlockDev &B, int d, int i, int j, int k, double F[NV])
+// faces of family d of block B in node-grid order: m = k*mplane + j*mpitch + i
+// with i <= ni (d = 0), j <= nj (d = 1), k <= nk (d = 2), the others inside
+__device__ __forceinline__ bool face_of(const BlockDev &B, int d, long long m, int &i, int &j, int &k)
 {
-    const int ndir = B.nk == 1 ? 2 : 3;
-    const int L[3] = {i - (d == 0), j - (d == 1), k - (d == 2)};
-    const int Rr[3] = {i, j, k};
-    const int e = d == 0 ? 1 : 0;
-    const int f = d == 2 ? 1 : 2;
-    const long long sv = B.L.sv;
-    const double *wv = B.wv;
-    const long long cL = cell_index(B.L, L[0], L[1], L[2]), cR = cell_index(B.L, i, j, k);
-    double pL[4], pR[4], dxi[4], deta[4], dzeta[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        pL[q] = wv[q * sv + cL];
-        pR[q] = wv[q * sv + cR];
-        dxi[q] = pR[q] - pL[q];
-        deta[q] = 0.0;
-        dzeta[q] = 0.0;
-    }
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const int a = t == 0 ? e : f;
-        if (a >= ndir) continue;
-        const int da = a == 0, db = a == 1, dc = a == 2;
-        const long long off = (long long)dc * B.L.sk + (long long)db * B.L.sj + da;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            // (-1) then (+1), the order of the sum in the reading above
-            double acc = -(wv[q * sv + cL - off] + wv[q * sv + cR - off]);
-            acc += wv[q * sv + cL + off] + wv[q * sv + cR + off];
-            if (t == 0)
-                deta[q] = 0.25 * acc;
-            else
-                dzeta[q] = 0.25 * acc;
-        }
-    }
-    int Lc[3] = {L[0], L[1], L[2]}, Rc[3] = {Rr[0], Rr[1], Rr[2]};
-    const BlockDev *bL = metric_cell(p.blocks, &B, Lc);
-    const BlockDev *bR = metric_cell(p.blocks, &B, Rc);
-    const long long mL = mindex(bL, Lc[0], Lc[1], Lc[2]), mR = mindex(bR, Rc[0], Rc[1], Rc[2]);
-    const double ivs = 1.0 / (bL->vol[mL] + bR->vol[mR]);
-    const int dirs[3] = {d, e, f};
-    double gx[3][3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        if (dirs[m] >= ndir) {
-            gx[m][0] = gx[m][1] = gx[m][2] = 0.0;
-            continue;
-        }
-        const double *sa = bL->sbar + (long long)(dirs[m] * 4) * bL->ml.mvolume + mL;
-        const double *sb = bR->sbar + (long long)(dirs[m] * 4) * bR->ml.mvolume + mR;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) gx[m][c] = (sa[c * bL->ml.mvolume] + sb[c * bR->ml.mvolume]) * ivs;
-    }
-    double grad[4][3];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) grad[q][c] = dxi[q] * gx[0][c] + deta[q] * gx[1][c] + dzeta[q] * gx[2][c];
-    const double mu = p.mu;
-    const double div = grad[0][0] + grad[1][1] + grad[2][2];
-    double tau[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            tau[a][c] = mu * (grad[a][c] + grad[c][a]) - (a == c ? 2.0 / 3.0 * mu * div : 0.0);
-    const double ub[3] = {0.5 * (pL[0] + pR[0]), 0.5 * (pL[1] + pR[1]), 0.5 * (pL[2] + pR[2])};
-    double theta[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-        theta[c] = ub[0] * tau[0][c] + ub[1] * tau[1][c] + ub[2] * tau[2][c] + p.kcond * grad[3][c];
-    // the face's area vector, unit normal x area
-    const long long mf = mindex(&B, i, j, k);
-    const double *fn = B.fn + (long long)(d * 4) * B.ml.mvolume + mf;
-    const double A = fn[3 * B.ml.mvolume];
-    const double S[3] = {fn[0] * A, fn[B.ml.mvolume] * A, fn[2 * B.ml.mvolume] * A};
-    F[0] = 0.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) F[1 + a] = tau[a][0] * S[0] + tau[a][1] * S[1] + tau[a][2] * S[2];
-    F[4] = theta[0] * S[0] + theta[1] * S[1] + theta[2] * S[2];
+    k = (int)(m / B.ml.mplane);
+    const long long r = m - (long long)k * B.ml.mplane;
+    j = (int)(r / B.ml.mpitch);
+    i = (int)(r - (long long)j * B.ml.mpitch);
+    return i < B.ni + (d == 0) && j < B.nj + (d == 1) && k < B.nk + (d == 2);
 }
 
-// R_nu = sum over a cell's faces of F_nu . S_out, dense interior layout
-__global__ void __launch_bounds__(256) vis_residual_kernel(VisBatch p)
+// grad xi_a at every d-face, a = d, e, f (the face's normal, then its two
+// tangential index directions): (Sbar_a(L) + Sbar_a(R)) / (|Omega_L| +
+// |Omega_R|), into gvis[(d * 9 + a * 3 + c) * mvolume + m].  Depends on the
+// boundary rules (the geometry a ghost cell carries): rerun when they change.
+__global__ void vis_metrics_kernel(const BlockDev *blocks)
+{
+    const int b = blockIdx.y, d = blockIdx.z;
+    const BlockDev &B = blocks[b];
+    const int ndir = B.nk == 1 ? 2 : 3;
+    if (d >= ndir) return;
+    const long long mv = B.ml.mvolume;
+    const int dirs[3] = {d, d == 0 ? 1 : 0, d == 2 ? 1 : 2};
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < mv; m += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        if (!face_of(B, d, m, i, j, k)) continue;
+        int Lc[3] = {i - (d == 0), j - (d == 1), k - (d == 2)}, Rc[3] = {i, j, k};
+        const BlockDev *bL = metric_cell(blocks, &B, Lc);
+        const BlockDev *bR = metric_cell(blocks, &B, Rc);
+        const long long mL = mindex(bL, Lc[0], Lc[1], Lc[2]), mR = mindex(bR, Rc[0], Rc[1], Rc[2]);
+        const double ivs = 1.0 / (bL->vol[mL] + bR->vol[mR]);
+        for (int a = 0; a < 3; ++a) {
+            const bool on = dirs[a] < ndir;
+            const double *sa = bL->sbar + (long long)(dirs[a] * 4) * bL->ml.mvolume + mL;
+            const double *sb = bR->sbar + (long long)(dirs[a] * 4) * bR->ml.mvolume + mR;
+            for (int c = 0; c < 3; ++c)
+                B.gvis[(long long)(d * 9 + a * 3 + c) * mv + m] =
+                    on ? (sa[c * bL->ml.mvolume] + sb[c * bR->ml.mvolume]) * ivs : 0.0;
+        }
+    }
+}
+
+// F_nu . S of every d-face into fvis[(d * NV + q) * mvolume + m], each face once
+__global__ void __launch_bounds__(256) vis_face_kernel(VisBatch p)
+{
+    const int b = blockIdx.y, d = blockIdx.z;
+    const BlockDev &B = p.blocks[b];
+    const int ndir = B.nk == 1 ? 2 : 3;
+    if (d >= ndir) return;
+    const long long mv = B.ml.mvolume;
+    const long long sv = B.L.sv;
+    const double *wv = B.wv;
+    const int e = d == 0 ? 1 : 0;
+    const int f = d == 2 ? 1 : 2;
+    const long long offd = d == 0 ? 1 : (d == 1 ? B.L.sj : B.L.sk);
+    const long long offe = e == 0 ? 1 : B.L.sj;
+    const long long offf = f == 1 ? B.L.sj : B.L.sk;
+    const bool has_f = f < ndir;
+    const double mu = p.mu, kcond = p.kcond;
+    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < mv; m += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        if (!face_of(B, d, m, i, j, k)) continue;
+        const long long cR = cell_index(B.L, i, j, k), cL = cR - offd;
+        double pL[4], pR[4], dxi[4], deta[4], dzeta[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            pL[q] = wv[q * sv + cL];
+            pR[q] = wv[q * sv + cR];
+            dxi[q] = pR[q] - pL[q];
+            // tangential central differences: (-1) then (+1)
+            double acc = -(wv[q * sv + cL - offe] + wv[q * sv + cR - offe]);
+            acc += wv[q * sv + cL + offe] + wv[q * sv + cR + offe];
+            deta[q] = 0.25 * acc;
+            dzeta[q] = 0.0;
+            if (has_f) {
+                double acc2 = -(wv[q * sv + cL - offf] + wv[q * sv + cR - offf]);
+                acc2 += wv[q * sv + cL + offf] + wv[q * sv + cR + offf];
+                dzeta[q] = 0.25 * acc2;
+            }
+        }
+        double gx[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gx[a][c] = B.gvis[(long long)(d * 9 + a * 3 + c) * mv + m];
+        double grad[4][3];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) grad[q][c] = dxi[q] * gx[0][c] + deta[q] * gx[1][c] + dzeta[q] * gx[2][c];
+        const double div = grad[0][0] + grad[1][1] + grad[2][2];
+        double tau[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                tau[a][c] = mu * (grad[a][c] + grad[c][a]) - (a == c ? 2.0 / 3.0 * mu * div : 0.0);
+        const double ub[3] = {0.5 * (pL[0] + pR[0]), 0.5 * (pL[1] + pR[1]), 0.5 * (pL[2] + pR[2])};
+        double theta[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            theta[c] = ub[0] * tau[0][c] + ub[1] * tau[1][c] + ub[2] * tau[2][c] + kcond * grad[3][c];
+        // the face's area vector, unit normal x area
+        const double *fn = B.fn + (long long)(d * 4) * mv + m;
+        const double A = fn[3 * mv];
+        const double S[3] = {fn[0] * A, fn[mv] * A, fn[2 * mv] * A};
+        double *out = B.fvis + (long long)(d * NV) * mv + m;
+        out[0] = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) out[(1 + a) * mv] = tau[a][0] * S[0] + tau[a][1] * S[1] + tau[a][2] * S[2];
+        out[4 * mv] = theta[0] * S[0] + theta[1] * S[1] + theta[2] * S[2];
+    }
+}
+
+// R_nu = sum over a cell's faces of F_nu . S_out (dense interior layout)
+__global__ void __launch_bounds__(256) vis_sum_kernel(VisBatch p)
 {
     const int b = blockIdx.y;
     const BlockDev &B = p.blocks[b];
     const long long nint = (long long)B.ni * B.nj * B.nk;
+    const long long mv = B.ml.mvolume;
     const int ndir = B.nk == 1 ? 2 : 3;
     for (long long rc = blockIdx.x * (long long)blockDim.x + threadIdx.x; rc < nint;
          rc += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(rc % B.ni);
         const int j = (int)((rc / B.ni) % B.nj);
         const int k = (int)(rc / ((long long)B.ni * B.nj));
+        const long long m = mindex(&B, i, j, k);
         double acc[NV] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int d = 0; d < ndir; ++d) {
-            double Flo[NV], Fhi[NV];
-            face_flux_nu(p, B, d, i, j, k, Flo);
-            face_flux_nu(p, B, d, i + (d == 0), j + (d == 1), k + (d == 2), Fhi);
+            const long long step = d == 0 ? 1 : (d == 1 ? B.ml.mpitch : B.ml.mplane);
+            const double *F = B.fvis + (long long)(d * NV) * mv + m;
 #pragma unroll
-            for (int q = 0; q < NV; ++q) acc[q] += Fhi[q] - Flo[q];
+            for (int q = 0; q < NV; ++q) acc[q] += F[q * mv + step] - F[q * mv];
         }
 #pragma unroll
         for (int q = 0; q < NV; ++q) B.rvis[q * nint + rc] = acc[q];
@@ -197,14 +229,26 @@ __global__ void __launch_bounds__(256) vis_residual_kernel(VisBatch p)
 
 }  // namespace
 
-cudaError_t launch_viscous(const VisBatch &p, long long max_state, long long max_cells, cudaStream_t s)
+cudaError_t launch_vis_metrics(const BlockDev *blocks, int nblocks, long long max_faces, cudaStream_t s)
 {
-    const unsigned gx1 = (unsigned)std::max<long long>(1, std::min<long long>((max_state + 255) / 256, 1024));
-    vis_prims_kernel<<<dim3(gx1, (unsigned)p.nblocks), 256, 0, s>>>(p);
+    const unsigned gx = (unsigned)std::max<long long>(1, std::min<long long>((max_faces + 255) / 256, 1024));
+    vis_metrics_kernel<<<dim3(gx, (unsigned)nblocks, 3), 256, 0, s>>>(blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_viscous(const VisBatch &p, long long max_state, long long max_faces, long long max_cells,
+                           cudaStream_t s)
+{
+    const unsigned g1 = (unsigned)std::max<long long>(1, std::min<long long>((max_state + 255) / 256, 1024));
+    vis_prims_kernel<<<dim3(g1, (unsigned)p.nblocks), 256, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const unsigned gx2 = (unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 1024));
-    vis_residual_kernel<<<dim3(gx2, (unsigned)p.nblocks), 256, 0, s>>>(p);
+    const unsigned g2 = (unsigned)std::max<long long>(1, std::min<long long>((max_faces + 255) / 256, 1024));
+    vis_face_kernel<<<dim3(g2, (unsigned)p.nblocks, 3), 256, 0, s>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned g3 = (unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 1024));
+    vis_sum_kernel<<<dim3(g3, (unsigned)p.nblocks), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
