@@ -169,14 +169,20 @@ sensei_status sensei_set_bc(sensei_grid *grid, int block, int face, int type, co
 
 /* Fill the two ghost layers of every boundary face of every block of the
  * states U[b] (Sec. 5, ghost cells on the GPU).  Edge and corner ghosts are
- * never read by the dimension-by-dimension stencil and are left alone. */
+ * never read by the dimension-by-dimension inviscid stencil and are left
+ * alone; with mu > 0 the block-edge ghosts (two indices outside the block,
+ * read by the viscous face gradients) are then filled by the rule of the
+ * lower face family (an i-face's rule at j- and k-ghost positions, a
+ * j-face's at k-ghost positions), which reads the other family's ghosts.
+ * Corner ghosts are never read. */
 sensei_status sensei_fill_ghosts(sensei_grid *grid, double *const *U, sensei_stream stream);
 
 /* Fill the ghosts of U, then write the residual R_h of Eq. residual for
  * every interior cell to R[b], a dense device array R[5][nk][nj][ni] (FP64):
- *   R = sum over the faces of the cell of F_hat . S_out  -  src
- * with F_hat the Roe flux (Harten entropy fix) of the MUSCL face states and
- * S_out the outward area vector.  src[b] (may be NULL, or src itself NULL)
+ *   R = sum over the faces of the cell of (F_hat - F_nu) . S_out  -  src
+ * with F_hat the Roe flux (Harten entropy fix) of the MUSCL face states,
+ * F_nu the viscous flux (zero for mu = 0) and S_out the outward area
+ * vector.  src[b] (may be NULL, or src itself NULL)
  * is |Omega| S_h per interior cell in the same layout as R.  Also records
  * the norms of this R (read them with sensei_norms). */
 sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const *R,
@@ -185,8 +191,10 @@ sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const
 /* One explicit Runge-Kutta step of all blocks, in place on U[b]
  * (Eq. runge_kutta with the 1/|Omega| of Eq. spatial_residual; evaluated in
  * the equivalent low-storage Shu-Osher form).  If cfl > 0 the step is
- * dt = cfl * min over cells of |Omega| / sum_d (|u . Sbar_d| + c |Sbar_d|)
- * evaluated on the device from U^n; otherwise `dt` (> 0) is used.  If
+ * dt = cfl * min over cells of |Omega| / sum_d (|u . Sbar_d| + c |Sbar_d|
+ *      + 4 max(4/3, gamma) mu / (Pr rho) |Sbar_d|^2 / |Omega|)
+ * evaluated on the device from U^n (the viscous term only for mu > 0);
+ * otherwise `dt` (> 0) is used.  If
  * dt_used is not NULL the step's dt is written there (device, 1 double).
  * The norms of R(U^n) and the sums of |Omega| U^n are recorded for
  * sensei_norms.  The ghost layers of U are refilled; on return they are
