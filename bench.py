@@ -92,6 +92,14 @@ def alg_bytes_per_cell(form, stage, two_d, stages=3):
     return b
 
 
+# DRAM bytes per interior cell and stencil launch, averaged over the three
+# SSPRK3 stage launches, from ncu dram__bytes_read.sum + dram__bytes_write.sum
+# of the 192^3 case of the periodic 3D workload (profiles/
+# stencil_traffic_periodic3d_192.md); the same tile schedule at 256^3, so the
+# traffic scales with the cells.  Re-measure when the kernel changes.
+MEASURED_TRAFFIC_B_PER_CELL = {"fp64": 241.1, "fp32_flux": 180.6}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -388,7 +396,9 @@ def main():
         achieved_tf = flops / (per_launch_ms / 1e3) / 1e12
         roofline = {
             "bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved_tf / fp64_peak, "traffic": None,
+            "frac": achieved_tf / fp64_peak,
+            "traffic": None if two_d else MEASURED_TRAFFIC_B_PER_CELL["fp64"] * cells,
+            "traffic_source": "ncu DRAM bytes per cell of the 192^3 capture x cells (3-stage average)",
             "kernel": "stencil_kernel<double,double> (fused MUSCL + Roe + residual + RK stage)",
             "peak_source": "derived FP64 vector peak: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
             "alg_flops_per_launch": flops, "kernel_ms_per_launch": per_launch_ms,
@@ -398,7 +408,10 @@ def main():
     else:
         roofline = {
             "bound": "hbm", "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_src,
+            "frac": hbm_gbs / peaks["hbm_gbs"],
+            "traffic": None if two_d else MEASURED_TRAFFIC_B_PER_CELL["fp32_flux"] * cells,
+            "traffic_source": "ncu DRAM bytes per cell of the 192^3 capture x cells (3-stage average)",
+            "peak_source": peak_src,
             "kernel": "stencil_kernel<float,double> (FP32 MUSCL + Roe on the FP64 state, FP64 update)",
             "alg_bytes_per_launch": byts, "kernel_ms_per_launch": per_launch_ms,
         }
