@@ -277,6 +277,22 @@ sensei_status sensei_profile_read(sensei_grid *grid, double *stencil_ms, long lo
 sensei_status sensei_residual_norms_noalloc(const double *R, int ni, int nj, int nk, double *l2, double *linf,
                                             sensei_stream stream);
 
+/* Test hooks of the bounded device waits (the paper has no counterpart;
+ * they exist so that failure detection can be tested without a GPU fault).
+ * The FP32 stencil waits on mbarriers for its bulk tile copies; every wait
+ * gives up after a limit, sets the device error word, waits once more for
+ * the copies in flight and leaves, and sensei_norms then returns
+ * SENSEI_ERR_TIMEOUT.
+ *   SENSEI_DEBUG_WAIT_LIMIT: the limit in SM clock cycles (0 = the default
+ *     2^31, about a second).
+ *   SENSEI_DEBUG_TX_EXTRA: bytes added to every tile phase's expected count
+ *     (0 = none).  A positive value makes every such wait run out: the data
+ *     arrives, the phase never completes.  For tests only.
+ * Apply to the following launches of this grid.  SENSEI_ERR_INVALID_ARG for
+ * an unknown key or a negative value. */
+enum { SENSEI_DEBUG_WAIT_LIMIT = 1, SENSEI_DEBUG_TX_EXTRA = 2 };
+sensei_status sensei_debug_set(sensei_grid *grid, int key, long long value);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *sensei_last_error(void);
 

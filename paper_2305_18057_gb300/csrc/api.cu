@@ -11,6 +11,7 @@
 // finalisation.  The blocks' static descriptions live in a device table in
 // the workspace, refreshed from the host copy when boundary rules or the
 // schedule change.
+#include <nvtx3/nvToolsExt.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -23,6 +24,16 @@
 using namespace sensei;
 
 namespace {
+
+// NVTX range for the duration of a scope (tracing with Nsight tools; a no-op
+// without an attached tool)
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
 
 thread_local char g_msg[512] = "";
 
@@ -257,6 +268,8 @@ struct sensei_grid {
     double *norms;      // 15 doubles, then the error word
     unsigned *err;
     bool dirty = true;          // descriptors changed since the last upload
+    long long wait_limit = 1LL << 31;   // bounded device waits (sensei_debug_set)
+    unsigned tx_extra = 0;
     bool stage_ghosts = false;  // fixed (inflow) ghosts of the stage buffers set
     int grid_mode = 0;          // 0: persistent (resident CTAs x SMs), 1: one CTA per item
     int ctas_cache[3] = {0, 0, 0};
@@ -454,6 +467,8 @@ void fill_params(BatchParams<R> &p, const sensei_grid *g, const StencilCall &c)
     p.half_eps = (R)0.5 * p.eps;
     p.cons = g->scheme.reconstruct_conserved ? 1 : 0;
     p.vis = c.vis ? 1 : 0;
+    p.wait_limit = g->wait_limit;
+    p.tx_extra = g->tx_extra;
     p.alpha = c.alpha;
     p.beta = c.beta;
     p.gdt = c.gdt;
@@ -603,6 +618,8 @@ sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, doub
             c.dprev = stage == 0 ? -1 : (stage - 1) % 2;
             c.dout = last ? -1 : stage % 2;
         }
+        TraceRange trace_stage(stage == 0 ? "rk stage 1" : stage == 1 ? "rk stage 2" : stage == 2 ? "rk stage 3"
+                                                                                    : "rk stage 4");
         if (viscous(grid)) {
             // R_nu of the stage input (its face ghosts are in place: filled
             // for U, pushed by the previous stage otherwise)
@@ -635,6 +652,23 @@ sensei_status check_step_args(sensei_grid *grid, double *const *U, int rk, doubl
 extern "C" {
 
 const char *sensei_last_error(void) { return g_msg; }
+
+sensei_status sensei_debug_set(sensei_grid *grid, int key, long long value)
+{
+    sensei_status st = check_grid(grid);
+    if (st != SENSEI_OK) return st;
+    if (value < 0) return fail(SENSEI_ERR_INVALID_ARG, "debug value must be >= 0");
+    if (key == SENSEI_DEBUG_WAIT_LIMIT) {
+        grid->wait_limit = value > 0 ? value : (1LL << 31);
+    } else if (key == SENSEI_DEBUG_TX_EXTRA) {
+        if (value > (1 << 16)) return fail(SENSEI_ERR_INVALID_ARG, "tx_extra above 65536 bytes");
+        grid->tx_extra = (unsigned)value;
+    } else {
+        return fail(SENSEI_ERR_INVALID_ARG, "unknown debug key %d", key);
+    }
+    g_msg[0] = 0;
+    return SENSEI_OK;
+}
 
 sensei_status sensei_profile_enable(sensei_grid *grid, int enable)
 {
@@ -685,6 +719,7 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
                                  const sensei_scheme *scheme, void *workspace, size_t workspace_bytes,
                                  sensei_stream stream, sensei_grid **out)
 {
+    TraceRange trace("sensei_create_grid");
     if (!out) return fail(SENSEI_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     Plan P;
@@ -841,6 +876,7 @@ sensei_status sensei_set_bc(sensei_grid *grid, int block, int face, int type, co
 
 sensei_status sensei_fill_ghosts(sensei_grid *grid, double *const *U, sensei_stream stream)
 {
+    TraceRange trace("sensei_fill_ghosts");
     sensei_status st = check_grid(grid);
     if (st == SENSEI_OK) st = check_states(grid, U, "U");
     if (st == SENSEI_OK) st = check_bcs(grid);
@@ -858,6 +894,7 @@ sensei_status sensei_fill_ghosts(sensei_grid *grid, double *const *U, sensei_str
 sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const *R, const double *const *src,
                               sensei_stream stream)
 {
+    TraceRange trace("sensei_residual");
     sensei_status st = check_grid(grid);
     if (st == SENSEI_OK) st = check_states(grid, U, "U");
     if (st == SENSEI_OK) st = check_states(grid, R, "R");
@@ -897,6 +934,7 @@ sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const
 sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double cfl, double dt, double *dt_used,
                              sensei_stream stream)
 {
+    TraceRange trace("sensei_rk_step");
     sensei_status st = check_step_args(grid, U, rk, cfl, dt);
     if (st != SENSEI_OK) return st;
     Device dev;
@@ -911,6 +949,7 @@ sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double
 sensei_status sensei_rk_step_local(sensei_grid *grid, double *const *U, int rk, double cfl, double *dt_min,
                                    sensei_stream stream)
 {
+    TraceRange trace("sensei_rk_step_local");
     sensei_status st = check_step_args(grid, U, rk, cfl, 0.0);
     if (st != SENSEI_OK) return st;
     if (!(cfl > 0.0)) return fail(SENSEI_ERR_INVALID_ARG, "local time stepping needs cfl > 0");
@@ -970,6 +1009,7 @@ sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int 
 
 sensei_status sensei_step_graph_launch(sensei_step_graph *graph, sensei_stream stream)
 {
+    TraceRange trace("sensei_step_graph_launch");
     if (!graph) return fail(SENSEI_ERR_INVALID_ARG, "graph is NULL");
     if (graph->grid->dirty || !graph->grid->stage_ghosts)
         return fail(SENSEI_ERR_STATE, "the grid's boundary rules or schedule changed since the graph was made");
@@ -990,6 +1030,7 @@ sensei_status sensei_step_graph_destroy(sensei_step_graph *graph)
 sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk_out, int *persistent_out,
                               sensei_stream stream)
 {
+    TraceRange trace("sensei_autotune");
     sensei_status st = check_grid(grid);
     if (st == SENSEI_OK) st = check_states(grid, U, "U");
     if (st == SENSEI_OK) st = check_bcs(grid);
@@ -1088,6 +1129,9 @@ sensei_status sensei_norms(sensei_grid *grid, double *l2, double *linf, double *
     if (errw) {
         CUDA_TRY(cudaMemsetAsync(grid->err, 0, sizeof(unsigned), s));
         CUDA_TRY(cudaStreamSynchronize(s));
+        if (errw & ERR_TIMEOUT)
+            return fail(SENSEI_ERR_TIMEOUT, "a bounded wait on an asynchronous tile copy gave up (error word 0x%x)",
+                        errw);
         return fail(SENSEI_ERR_NONPHYSICAL, "a kernel met rho <= 0, p <= 0 or a non-finite state (error word 0x%x)",
                     errw);
     }

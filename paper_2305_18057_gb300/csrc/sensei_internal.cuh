@@ -129,6 +129,8 @@ struct BatchParams {
     R gm1, kg, c1, c2, half_eps;   // gamma - 1, gamma / (gamma - 1), eps (1 -+ kappa) / 4, eps / 2 in R
     int cons;
     int vis;                // subtract the viscous residual B.rvis
+    long long wait_limit;   // bounded mbarrier waits: clock cycles before giving up
+    unsigned tx_extra;      // test hook: bytes added to every tile phase's expected count
     double alpha, beta, gdt;
     const double *dt_slot;  // dt = dt_scale * *dt_slot
     double dt_scale;

@@ -23,7 +23,7 @@
 //   * the own column's k-window (primitives of planes k..k+2, the plus
 //     state of plane k, the flux of its lower k-face) stays in registers,
 //     fed by a register prefetch of the raw state three planes ahead.
-// Every wait on an mbarrier is bounded (about a second of clock cycles);
+// Every wait on an mbarrier is bounded (by default 2^31 clock cycles);
 // on expiry the CTA sets ERR_TIMEOUT, waits (bounded) for its copies in
 // flight and leaves.
 #pragma once
@@ -89,14 +89,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// wait for the phase of the given parity to complete; false after 2^31
-// clock cycles (about one second at 2 GHz)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// wait for the phase of the given parity to complete; false after `limit`
+// clock cycles (2^31 by default, about one second at 2 GHz)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -119,9 +119,10 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uin
 // and the plane's face-metric record.
 template <typename TS>
 __device__ __forceinline__ void issue_plane(const TS *in, const StateLayout &L, int i0, int j0, int k, int nrows,
-                                            int len, const float *rec, TS *raw, float *met, uint32_t bar, int lane)
+                                            int len, const float *rec, TS *raw, float *met, uint32_t bar, int lane,
+                                            unsigned tx_extra)
 {
-    const uint32_t bytes = (uint32_t)(NV * nrows * len * (int)sizeof(TS) + REC * (int)sizeof(float));
+    const uint32_t bytes = (uint32_t)(NV * nrows * len * (int)sizeof(TS) + REC * (int)sizeof(float)) + tx_extra;
     if (lane == 0) {
         fence_proxy_async();
         mbar_arrive_expect_tx(bar, bytes);
@@ -272,7 +273,8 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
         // each issued plane is waited for within its item)
         int cb = 0;
         if (warp == 0)
-            issue_plane<TS>(in, L, i0, j0, k0, nrows, len, rec0 + k0 * rec_stride, sRaw, sMet, bar0, lane);
+            issue_plane<TS>(in, L, i0, j0, k0, nrows, len, rec0 + k0 * rec_stride, sRaw, sMet, bar0, lane,
+                            p.tx_extra);
 
         // FP64 norm partials: double-single sum of squares, FP32 max, FP64
         // conservation sums (FP64 stage input only)
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
             // ---- P0: wait for the plane's tile, primitives into sW
             const TS *raw = sRaw + cb * NV * TPLANE;
             const float *met = sMet + cb * REC;
-            const bool ok = mbar_wait(bar0 + 8 * cb, (phase >> cb) & 1u);
+            const bool ok = mbar_wait(bar0 + 8 * cb, (phase >> cb) & 1u, p.wait_limit);
             phase ^= 1u << cb;
             if (TWO_D) {
                 for (int e = t; e < TPLANE; e += NTHREADS) {
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
                 // been waited for
                 if (t == 0) {
                     atomicOr(p.err, ERR_TIMEOUT);
-                    mbar_wait(bar0 + 8 * cb, ((phase >> cb) & 1u) ^ 1u);
+                    mbar_wait(bar0 + 8 * cb, ((phase >> cb) & 1u) ^ 1u, p.wait_limit);
                 }
                 failed = true;
                 break;
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
                 const int nb = cb ^ 1;
                 if (warp == 0)
                     issue_plane<TS>(in, L, i0, j0, k + 1, nrows, len, rec0 + (k + 1) * rec_stride,
-                                    sRaw + nb * NV * TPLANE, sMet + nb * REC, bar0 + 8 * nb, lane);
+                                    sRaw + nb * NV * TPLANE, sMet + nb * REC, bar0 + 8 * nb, lane, p.tx_extra);
             }
 
             // ---- P1: fluxes: the j-face below the own cell (to sFj); warp 0

@@ -30,7 +30,8 @@ NV = 5
 EXPORTS = ("sensei_workspace_size", "sensei_create_grid", "sensei_destroy_grid", "sensei_state_layout",
            "sensei_set_bc", "sensei_fill_ghosts", "sensei_residual", "sensei_rk_step", "sensei_norms",
            "sensei_rk_step_local", "sensei_step_graph_create", "sensei_step_graph_launch", "sensei_step_graph_destroy", "sensei_autotune",
-           "sensei_profile_enable", "sensei_profile_read", "sensei_residual_norms_noalloc", "sensei_last_error")
+           "sensei_profile_enable", "sensei_profile_read", "sensei_residual_norms_noalloc", "sensei_debug_set",
+           "sensei_last_error")
 
 
 class BlockDesc(C.Structure):
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH):
     L.sensei_profile_enable.argtypes = [vp, C.c_int]
     L.sensei_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
     L.sensei_residual_norms_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, dp, vp]
+    L.sensei_debug_set.argtypes = [vp, C.c_int, C.c_longlong]
     L.sensei_last_error.argtypes = []
     L.sensei_last_error.restype = C.c_char_p
     for name in EXPORTS[:-1]:
@@ -196,6 +198,14 @@ def sensei_profile_read(grid, reset=True):
     ms, ns, nk = C.c_double(), C.c_longlong(), C.c_longlong()
     _check(load().sensei_profile_read(grid, C.byref(ms), C.byref(ns), C.byref(nk), int(reset)))
     return ms.value, ns.value, nk.value
+
+
+DEBUG_WAIT_LIMIT, DEBUG_TX_EXTRA = 1, 2
+
+
+def sensei_debug_set(grid, key, value):
+    """Test hooks of the bounded device waits (see include/sensei.h)."""
+    _check(load().sensei_debug_set(grid, int(key), int(value)))
 
 
 def sensei_residual_norms_noalloc(R_ptr, ni, nj, nk, stream_ptr):
@@ -317,6 +327,9 @@ class Grid:
 
     def autotune(self, Us):
         return sensei_autotune(self.handle, [U.data_ptr() for U in Us], self.sptr)
+
+    def debug_set(self, key, value):
+        sensei_debug_set(self.handle, key, value)
 
     def profile(self, enable=True):
         sensei_profile_enable(self.handle, enable)

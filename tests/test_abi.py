@@ -84,6 +84,7 @@ def test_invalid_arguments_rejected_on_host(sensei):
     assert L.sensei_rk_step(None, None, 1, 0.5, 0.0, None, None) == sensei.ERR_INVALID_ARG
     assert L.sensei_norms(None, None, None, None, None) == sensei.ERR_INVALID_ARG
     assert L.sensei_destroy_grid(None) == sensei.ERR_INVALID_ARG
+    assert L.sensei_debug_set(None, sensei.DEBUG_WAIT_LIMIT, 0) == sensei.ERR_INVALID_ARG
     lay = sensei.Layout()
     assert L.sensei_state_layout(None, 0, C.byref(lay)) == sensei.ERR_INVALID_ARG
     # a grid cannot be created without a workspace (checked before any CUDA call)
