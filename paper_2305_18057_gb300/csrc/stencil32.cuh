@@ -414,28 +414,11 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
                                     sRaw + nb * NV * TPLANE, sMet + nb * REC, bar0 + 8 * nb, lane, p.tx_extra);
             }
 
-            // ---- P1: fluxes: the j-face below the own cell (to sFj); warp 0
-            //      also the tile's top j-faces, warp 1 its right i-faces (to
-            //      sFiE); the own column's upper k-face and the i-face left
-            //      of the own cell stay in registers
-            {
-                float F[NV];
-                line_flux<LIM>(sW + tj * TW + ti + 2, TW, met + REC_I + tj * TI + ti, (TJ + 1) * TI, gm1, kg, fix,
-                               c1, c2, half_eps, cons, F);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) sFj[v * FJV + tj * TI + ti] = F[v];
-                if (warp == 0) {
-                    line_flux<LIM>(sW + TJ * TW + lane + 2, TW, met + REC_I + TJ * TI + lane, (TJ + 1) * TI, gm1, kg,
-                                   fix, c1, c2, half_eps, cons, F);
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) sFj[v * FJV + TJ * TI + lane] = F[v];
-                } else if (warp == 1 && lane < TJ) {
-                    line_flux<LIM>(sW + (lane + 2) * TW + TI, 1, met + lane * (TI + 1) + TI, TJ * (TI + 1), gm1, kg,
-                                   fix, c1, c2, half_eps, cons, F);
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) sFiE[v * TJ + lane] = F[v];
-                }
-            }
+            // ---- P1: fluxes: the own column's upper k-face (registers);
+            //      then, through one copy of the MUSCL + Roe code, the j-face
+            //      below the own cell (to sFj), the tile's top j-faces (warp
+            //      0) and right i-faces (warp 1) (to sFj, sFiE), and the
+            //      i-face left of the own cell (registers)
             float Fkp[NV], Ppn[NV];
             if (!TWO_D) {
                 float Rk[NV];
@@ -447,8 +430,53 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
                 face_flux(Pp, Rk, mk[0], mk[TJ * TI], mk[2 * TJ * TI], mk[3 * TJ * TI], gm1, kg, fix, cons, Fkp);
             }
             float Fi[NV];
-            line_flux<LIM>(sW + (tj + 2) * TW + ti, 1, met + tj * (TI + 1) + ti, TJ * (TI + 1), gm1, kg, fix, c1, c2,
-                           half_eps, cons, Fi);
+#pragma unroll 1
+            for (int job = 0; job < 3; ++job) {
+                const float *w;
+                const float *mt;
+                int st, mst;
+                float *dst = nullptr;
+                int dstv = 0;
+                if (job == 0) {
+                    w = sW + tj * TW + ti + 2;
+                    st = TW;
+                    mt = met + REC_I + tj * TI + ti;
+                    mst = (TJ + 1) * TI;
+                    dst = sFj + tj * TI + ti;
+                    dstv = FJV;
+                } else if (job == 1) {
+                    if (warp > 1 || (warp == 1 && lane >= TJ)) continue;
+                    if (warp == 0) {
+                        w = sW + TJ * TW + lane + 2;
+                        st = TW;
+                        mt = met + REC_I + TJ * TI + lane;
+                        mst = (TJ + 1) * TI;
+                        dst = sFj + TJ * TI + lane;
+                        dstv = FJV;
+                    } else {
+                        w = sW + (lane + 2) * TW + TI;
+                        st = 1;
+                        mt = met + lane * (TI + 1) + TI;
+                        mst = TJ * (TI + 1);
+                        dst = sFiE + lane;
+                        dstv = TJ;
+                    }
+                } else {
+                    w = sW + (tj + 2) * TW + ti;
+                    st = 1;
+                    mt = met + tj * (TI + 1) + ti;
+                    mst = TJ * (TI + 1);
+                }
+                float F[NV];
+                line_flux<LIM>(w, st, mt, mst, gm1, kg, fix, c1, c2, half_eps, cons, F);
+                if (dst) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) dst[v * dstv] = F[v];
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Fi[v] = F[v];
+                }
+            }
             __syncthreads();
 
             // ---- P2: residual, update, ghost push, norm partials
