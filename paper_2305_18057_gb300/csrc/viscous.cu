@@ -130,7 +130,7 @@ __global__ void vis_metrics_kernel(const BlockDev *blocks)
 }
 
 // F_nu . S of every d-face into fvis[(d * NV + q) * mvolume + m], each face once
-__global__ void __launch_bounds__(256) vis_face_kernel(VisBatch p)
+__global__ void __launch_bounds__(256, 2) vis_face_kernel(VisBatch p)
 {
     const int b = blockIdx.y, d = blockIdx.z;
     const BlockDev &B = p.blocks[b];
