@@ -304,6 +304,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_ranks(ms, units, device):
+    """Whole-job figures over the ranks of the default process group: the
+    slowest rank's time (ms) and the sum of the cell updates every rank
+    performed.  Every rank calls it (a collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return t.item(), u.item()
+
+
 def config_for(name):
     return {"workload": WORKLOADS[name], "l2": "inputs larger than L2 (state >= 0.7 GB)" if name in ("c3", "c4", "c5")
             else "inputs L2-resident (noted, not an HBM claim)", "parallelism": "replicas"}
@@ -375,11 +388,7 @@ def main():
         clk = clocks.stop()
     units = cells * stages * args.steps
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        u = torch.tensor([float(units)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        ms, units = t.item(), u.item()
+        ms, units = aggregate_ranks(ms, units, "cuda")
     value = units / (ms / 1e3)
 
     # the dominant kernel: the fused stencil/update kernel
@@ -447,9 +456,7 @@ def main():
     torch.cuda.synchronize()
     ems = e0.elapsed_time(e1)
     if world > 1:
-        t = torch.tensor([ems], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = t.item()
+        ems, _ = aggregate_ranks(ems, 0, "cuda")
     state_bytes = sum(U.numel() * 8 for U in Us)
     line["e2e"] = {"value": units / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                    "d2h_bytes_per_step": state_bytes + 15 * 8}
