@@ -209,22 +209,27 @@ __device__ __forceinline__ void face_states(R wm, R w0, R wp, R c1, R c2, R half
         plus = w0 + (c1 * dm + c2 * dp);
         minus = w0 - (c2 * dm + c1 * dp);
     } else {
-        R d;
+        // the limited slope sigma, then W +- (eps / 2) sigma as one fused
+        // multiply-add each
+        R sig, scale;
         if (LIM == SENSEI_LIM_MINMOD) {
             // minmod: the smaller difference if both have the same sign (a
             // zero difference gives 0 either way); sign and magnitude tests
             // on the bit patterns
             R m = abs_le(dm, dp) ? dm : copysign(dp, dm);
-            d = same_sign(dm, dp) ? half_eps * m : R(0);
+            sig = same_sign(dm, dp) ? m : R(0);
+            scale = half_eps;
         } else {
-            // van Leer: 2 dm dp / (dm + dp) when dm dp > 0; the reciprocal
-            // only scales a limited slope, one Newton step suffices
+            // van Leer: 2 dm dp / (dm + dp) when dm dp > 0 (the factor 2
+            // joins eps / 2); the reciprocal only scales a limited slope,
+            // one Newton step suffices
             R pr = dm * dp;
             R r = rcp_t<R, 1>(dm + dp);
-            d = positive(pr) ? (pr * r) * (R(2) * half_eps) : R(0);
+            sig = positive(pr) ? pr * r : R(0);
+            scale = R(2) * half_eps;
         }
-        plus = w0 + d;
-        minus = w0 - d;
+        plus = fma(sig, scale, w0);
+        minus = fma(-sig, scale, w0);
     }
 }
 
