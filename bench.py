@@ -9,7 +9,7 @@ substeps counted is 1e-6 times this, Sec. 6 Eq. ssspnt).
 
 One JSON line on rank 0.  A step is one full SSPRK3 step (ghost fill, time
 step reduction, three fused stencil/update stages, norm finalisation) over
-the whole grid.  With N > 1 (torchrun) every rank advances its own replica
+the whole grid, replayed as a CUDA graph (--eager: launched one by one).  With N > 1 (torchrun) every rank advances its own replica
 of the grid on its own GPU: the method has no data-path exchange between
 GPUs in this build ("replicas only"), so scaling is weak and the value is the
 sum over ranks of the cells each advanced, over the slowest rank's time.
@@ -335,7 +335,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-perf-model", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="grid size override (c3, c5): small profiling cases")
-    ap.add_argument("--graph", action="store_true", help="time CUDA-graph replays of the step (default for c4)")
+    ap.add_argument("--eager", action="store_true",
+                    help="time eager launches instead of CUDA-graph replays of the step")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -361,10 +362,11 @@ def main():
     cells = w.cells
     rk = sensei.RK3_SSP
     stages = 3
-    # the batched multiblock workload runs FP32 flux on the FP64 state, as a
-    # CUDA graph per step; the others FP64 eagerly (mixed forms as variants)
+    # the batched multiblock workload runs FP32 flux on the FP64 state, the
+    # others FP64 (mixed forms as variants); the main line replays a CUDA
+    # graph of one step
     main_prec = sensei.FP32_FLUX if args.workload == "c4" else sensei.FP64
-    use_graph = args.graph or args.workload == "c4"
+    use_graph = not args.eager
     g, Us, schedule = gpu_setup(w, main_prec)
     for _ in range(args.warmup):
         g.rk_step(Us, rk, cfl=w.cfl)

@@ -123,6 +123,20 @@ __device__ __forceinline__ bool positive(double x) { return __double_as_longlong
 __device__ __forceinline__ bool positive(float x) { return __float_as_int(x) > 0; }
 __device__ __forceinline__ bool same_sign(double a, double b) { return (__double2hiint(a) ^ __double2hiint(b)) >= 0; }
 __device__ __forceinline__ bool same_sign(float a, float b) { return (__float_as_int(a) ^ __float_as_int(b)) >= 0; }
+// 0 < x < infinity (finite, positive, not NaN) from the bit pattern
+__device__ __forceinline__ bool positive_finite(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool positive_finite(float x)
+{
+    const int b = __float_as_int(x);
+    return b > 0 && b < 0x7f800000;
+}
+// a < b for a, b >= 0 (or NaN, which compares false) by the bit patterns
+__device__ __forceinline__ bool lt_nonneg(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+__device__ __forceinline__ bool lt_nonneg(float a, float b) { return __float_as_int(a) < __float_as_int(b); }
 // |a| <= |b| by the bit patterns of the magnitudes
 __device__ __forceinline__ bool abs_le(double a, double b)
 {
@@ -190,7 +204,7 @@ __device__ __forceinline__ bool to_prim(const R q[NV], R gm1, R w[NV])
     w[2] = v;
     w[3] = ww;
     w[4] = p;
-    return q[0] > R(0) && p > R(0) && q[0] < R(INFINITY) && p < R(INFINITY);
+    return positive_finite(q[0]) && positive_finite(p);
 }
 
 // MUSCL extrapolation to the two faces of one cell (Eq. flux), per variable:
@@ -277,8 +291,9 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     R l1 = fabs(vn - a), l3 = fabs(vn + a);
     const R l2 = fabs(vn);
     const R delta = fix * a;
-    if (l1 < delta) l1 = R(0.5) * (l1 * l1 * (ia / fix) + delta);
-    if (l3 < delta) l3 = R(0.5) * (l3 * l3 * (ia / fix) + delta);
+    // |lambda| < delta on the integer pipe (both are >= 0)
+    if (lt_nonneg(l1, delta)) l1 = R(0.5) * (l1 * l1 * (ia / fix) + delta);
+    if (lt_nonneg(l3, delta)) l3 = R(0.5) * (l3 * l3 * (ia / fix) + delta);
     const R rad = rho * a * dvn;
     const R c1w = l1 * (R(0.5) * (dp - rad) * ia2);
     const R c3w = l3 * (R(0.5) * (dp + rad) * ia2);
