@@ -447,7 +447,7 @@ __device__ __noinline__ void push_ghosts(const BatchParams<R> &p, const BlockDev
     }
 }
 
-template <typename R, typename TS, int LIM, bool TWO_D>
+template <typename R, typename TS, int LIM, bool TWO_D, bool PART>
 __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(const __grid_constant__ BatchParams<R> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                         } else {
                             p.rout[b][v * nint + rc] = r;
                         }
-                        if (p.partials) {
+                        if (PART && p.partials) {
                             nsq[v] = fma(r, r, nsq[v]);
                             nmax[v] = fmax(nmax[v], fabs(r));
                             ncons[v] = fma(vol, uin, ncons[v]);
@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
         }
 
         // ---- FP64 norm partials of this item, fixed-order reduction
-        if (p.partials) {
+        if (PART && p.partials) {
             const int lane = t & 31, warp = t >> 5;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -777,18 +777,20 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     }
 }
 
-template <typename R, typename TS>
+// PART: the variant that accumulates the norm partials (the first stage of
+// a step, residual evaluations); the other stages run without its registers
+template <typename R, typename TS, bool PART>
 struct StencilLauncher {
     using Fn = void (*)(const BatchParams<R>);
     static Fn pick(int limiter, bool two_d)
     {
         switch (limiter) {
-        case SENSEI_LIM_NONE: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_NONE, true>
-                                           : stencil_kernel<R, TS, SENSEI_LIM_NONE, false>;
-        case SENSEI_LIM_MINMOD: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_MINMOD, true>
-                                             : stencil_kernel<R, TS, SENSEI_LIM_MINMOD, false>;
-        default: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_VANLEER, true>
-                              : stencil_kernel<R, TS, SENSEI_LIM_VANLEER, false>;
+        case SENSEI_LIM_NONE: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_NONE, true, PART>
+                                           : stencil_kernel<R, TS, SENSEI_LIM_NONE, false, PART>;
+        case SENSEI_LIM_MINMOD: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_MINMOD, true, PART>
+                                             : stencil_kernel<R, TS, SENSEI_LIM_MINMOD, false, PART>;
+        default: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_VANLEER, true, PART>
+                              : stencil_kernel<R, TS, SENSEI_LIM_VANLEER, false, PART>;
         }
     }
     static cudaError_t prepare(Fn fn)
