@@ -40,13 +40,15 @@ namespace sensei {
 template <typename R>
 struct SmemLayout {
     // sW[NV][TJ+4][TI+4], sP_i[2][NV][TJ][TI+2], sP_j[2][NV][TJ+2][TI],
-    // sF_i[NV][TJ][TI+1], sF_j[NV][TJ+1][TI], reduction scratch
+    // sF_i[NV][TJ][TI+1], sF_j[NV][TJ+1][TI], sK[2][NV][NTHREADS] (each
+    // thread's own column at planes k+1 and k+2), reduction scratch
     static constexpr int W = NV * (TJ + 4) * (TI + 4);
     static constexpr int PI = 2 * NV * TJ * (TI + 2);
     static constexpr int PJ = 2 * NV * (TJ + 2) * TI;
     static constexpr int FI = NV * TJ * (TI + 1);
     static constexpr int FJ = NV * (TJ + 1) * TI;
-    static constexpr int elems = W + PI + PJ + FI + FJ;
+    static constexpr int K = 2 * NV * NTHREADS;
+    static constexpr int elems = W + PI + PJ + FI + FJ + K;
     static constexpr int red_doubles = 3 * NV * (NTHREADS / 32);
     static constexpr size_t bytes = sizeof(R) * (size_t)elems + sizeof(double) * red_doubles + 16;
 };
@@ -457,7 +459,8 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     R *sPj = sPi + SL::PI;
     R *sFi = sPj + SL::PJ;
     R *sFj = sFi + SL::FI;
-    double *sRed = reinterpret_cast<double *>(sFj + SL::FJ + ((SL::elems * sizeof(R)) % 8 ? 1 : 0));
+    R *sK = sFj + SL::FJ;
+    double *sRed = reinterpret_cast<double *>(sK + SL::K + ((SL::elems * sizeof(R)) % 8 ? 1 : 0));
     __shared__ BlockDev sB;
 
     constexpr int WP = TI + 4;                 // sW row pitch
@@ -518,13 +521,16 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
 #pragma unroll
         for (int v = 0; v < NV; ++v) nsq[v] = nmax[v] = ncons[v] = 0.0;
 
-        // per-thread k-window of the own column: centre plane, the two
-        // above, the plus-side k-state of the centre plane, the flux of its
-        // lower k-face
-        R Wc[NV], W1[NV], W2[NV], Pp[NV], Fkm[NV];
+        // per-thread k-window of the own column: the centre plane (in
+        // registers until the plane's P0 puts it in sW), planes k+1 and k+2
+        // in sK[kb] and sK[kb ^ 1] (each thread its own entries), the
+        // plus-side k-state of the centre plane and the flux of its lower
+        // k-face in registers
+        R Wc[NV], Pp[NV], Fkm[NV];
+        int kb = 0;
         if (!TWO_D) {
             R q[NV];
-            R Wm2[NV], Wm1[NV];
+            R Wm2[NV], Wm1[NV], W1[NV], W2[NV];
             ld.raw(ci, cj, k0 - 2, q);
             to_recon(q, gm1, cons, false, p.err, Wm2);
             ld.raw(ci, cj, k0 - 1, q);
@@ -546,6 +552,11 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
             const R *f2 = fm + 8 * ml.mvolume;
             face_flux(Lk, Rk, f2[fk], f2[ml.mvolume + fk], f2[2 * ml.mvolume + fk], f2[3 * ml.mvolume + fk], gm1, kg,
                       p.fix, cons, Fkm);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                sK[v * NTHREADS + t] = W1[v];
+                sK[(NV + v) * NTHREADS + t] = W2[v];
+            }
         }
 
         for (int k = k0; k < k1; ++k) {
@@ -678,7 +689,9 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                 // right = minus state of plane k+1
                 R Rk[NV];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) face_states<R, LIM>(Wc[v], W1[v], W2[v], c1, c2, half_eps, Ppn[v], Rk[v]);
+                for (int v = 0; v < NV; ++v)
+                    face_states<R, LIM>(W_at(v, tj, ti), sK[(kb * NV + v) * NTHREADS + t],
+                                        sK[((kb ^ 1) * NV + v) * NTHREADS + t], c1, c2, half_eps, Ppn[v], Rk[v]);
                 const long long fk = (long long)(k + 1) * ml.mplane + (long long)min(cj, B.nj - 1) * ml.mpitch +
                                      min(ci, B.ni - 1);
                 const R *f2 = fm + 8 * ml.mvolume;
@@ -737,11 +750,14 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                 for (int v = 0; v < NV; ++v) {
                     Fkm[v] = Fkp[v];
                     Pp[v] = Ppn[v];
-                    Wc[v] = W1[v];
-                    W1[v] = W2[v];
+                    Wc[v] = sK[(kb * NV + v) * NTHREADS + t];
                     q[v] = pre[v];
                 }
-                to_recon(q, gm1, cons, col_valid && k + 3 < B.nk, p.err, W2);
+                R w3[NV];
+                to_recon(q, gm1, cons, col_valid && k + 3 < B.nk, p.err, w3);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) sK[(kb * NV + v) * NTHREADS + t] = w3[v];
+                kb ^= 1;
             }
         }
 
