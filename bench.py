@@ -551,6 +551,17 @@ def main():
         v, secs, sample, _ = oracle_sample(args.workload, 3 if args.workload in ("c3", "c5") else 2, 0, depth)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                                 "seconds": secs, "host_cpus": os.cpu_count()}
+    # NEXT row f4 by the model of Sec. 6 (Eq. hete with alpha = 0): adding C
+    # host cores to one GPU that is r_gc times one core (the oracle, as a
+    # stand-in CPU worker) shrinks the interior term by (r_gc + C) / r_gc
+    if "perf_model" in line and "cpu_baseline" in line:
+        r_gc = value / line["cpu_baseline"]["value"]
+        cores = os.cpu_count() or 1
+        line["perf_model"]["heterogeneous"] = {
+            "r_gc_vs_oracle_core": r_gc, "host_cores": cores,
+            "cpu_share_of_cells": cores / (r_gc + cores),
+            "model_speedup_vs_gpu_only": (r_gc + cores) / r_gc,
+            "note": "Eq. hete, interior term, ideal overlap; the CPU worker would be the plain oracle (not run)"}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
