@@ -479,7 +479,7 @@ def main():
         torch.cuda.synchronize()
         line["variants"] = {}
         for vname, prec in (("fp64", sensei.FP64), ("fp32_flux", sensei.FP32_FLUX),
-                            ("fp32_store", sensei.FP32_STORE)):
+                            ("fp32_store", sensei.FP32_STORE), ("df64", sensei.DF64)):
             if prec == main_prec:
                 continue
             gv, Uv, sched_v = gpu_setup(w, prec)
@@ -495,7 +495,8 @@ def main():
             rho_l2 = math.sqrt(sum(e[0] ** 2 for e in errs)) / math.sqrt(sum(e[1] ** 2 for e in errs))
             vv = cells * stages * args.steps / (msv / 1e3)
             stv = profv[0] / max(profv[1], 1)
-            bv = cells * sum(alg_bytes_per_cell(vname, s_, two_d) for s_ in range(stages)) / stages
+            bv = cells * sum(alg_bytes_per_cell("fp64" if vname == "df64" else vname, s_, two_d)
+                             for s_ in range(stages)) / stages
             line["variants"][vname] = {
                 "value": vv, "unit": UNIT, "ms_per_step": msv / args.steps,
                 "speedup_vs_fp64": (vv / value if main_prec == sensei.FP64 else None) if world == 1 else None,

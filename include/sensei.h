@@ -68,7 +68,11 @@ typedef enum {
 typedef enum {
     SENSEI_FP64 = 0,        /* FP64 state, FP64 flux */
     SENSEI_FP32_FLUX = 1,   /* FP64 state; reconstruction and flux in FP32 */
-    SENSEI_FP32_STORE = 2   /* FP64 master state U^n; FP32 stage states and FP32 flux */
+    SENSEI_FP32_STORE = 2,  /* FP64 master state U^n; FP32 stage states and FP32 flux */
+    SENSEI_DF64 = 3         /* FP64 state; reconstruction and flux in double-float arithmetic
+                             * (pairs of FP32 numbers, about 48 significant bits, computed on
+                             * the FP32 pipe); not in the paper: an FP64-class alternative for
+                             * GPUs whose FP64 pipe is narrow */
 } sensei_precision;
 
 /* Ghost-cell rules, 2 ghost layers per boundary face. */

@@ -91,7 +91,7 @@ sensei_status check_scheme(const sensei_scheme *s)
     if (!(s->gamma > 1.0)) return fail(SENSEI_ERR_INVALID_ARG, "gamma must be > 1 (got %g)", s->gamma);
     if (s->limiter < SENSEI_LIM_NONE || s->limiter > SENSEI_LIM_VANLEER)
         return fail(SENSEI_ERR_INVALID_ARG, "unknown limiter %d", s->limiter);
-    if (s->precision < SENSEI_FP64 || s->precision > SENSEI_FP32_STORE)
+    if (s->precision < SENSEI_FP64 || s->precision > SENSEI_DF64)
         return fail(SENSEI_ERR_INVALID_ARG, "unknown precision %d", s->precision);
     if (!(s->entropy_fix >= 0.0)) return fail(SENSEI_ERR_INVALID_ARG, "entropy_fix must be >= 0");
     if (!(s->eps >= 0.0 && s->eps <= 1.0)) return fail(SENSEI_ERR_INVALID_ARG, "eps must lie in [0, 1]");
@@ -99,8 +99,8 @@ sensei_status check_scheme(const sensei_scheme *s)
     if (!(s->mu >= 0.0 && s->mu < INFINITY)) return fail(SENSEI_ERR_INVALID_ARG, "mu must be finite and >= 0");
     if (s->mu > 0.0 && !(s->prandtl > 0.0 && s->prandtl < INFINITY))
         return fail(SENSEI_ERR_INVALID_ARG, "prandtl must be finite and > 0 when mu > 0");
-    if (s->mu > 0.0 && s->precision != SENSEI_FP64)
-        return fail(SENSEI_ERR_UNSUPPORTED, "the viscous flux runs in FP64 precision only");
+    if (s->mu > 0.0 && s->precision != SENSEI_FP64 && s->precision != SENSEI_DF64)
+        return fail(SENSEI_ERR_UNSUPPORTED, "the viscous flux runs with the FP64 state update only (FP64, DF64)");
     return SENSEI_OK;
 }
 
@@ -152,7 +152,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
                     &P.off_wv, &P.off_rvis, &P.off_fvis, &P.off_gvis,
                     &P.off_stage})
         v->resize(nblocks);
-    const bool f32 = scheme->precision != SENSEI_FP64;
+    const bool f32 = scheme->precision == SENSEI_FP32_FLUX || scheme->precision == SENSEI_FP32_STORE;
     P.two_d = blocks[0].nk == 1;
     long long tiles_total = 0;
     for (int b = 0; b < nblocks; ++b) {
@@ -272,7 +272,7 @@ struct sensei_grid {
     unsigned tx_extra = 0;
     bool stage_ghosts = false;  // fixed (inflow) ghosts of the stage buffers set
     int grid_mode = 0;          // 0: persistent (resident CTAs x SMs), 1: one CTA per item
-    int ctas_cache[3] = {0, 0, 0};
+    int ctas_cache[4] = {0, 0, 0, 0};
     // instrumentation
     bool prof = false;
     std::vector<cudaEvent_t> ev;   // start/end pairs
@@ -317,9 +317,11 @@ sensei_status check_bcs(const sensei_grid *g)
     return SENSEI_OK;
 }
 
+// 0 FP64, 1 FP32 arithmetic on an FP64 input, 2 on an FP32 input, 3 double-float
 int precision_kind(const sensei_grid *g, bool in_f32)
 {
     if (g->scheme.precision == SENSEI_FP64) return 0;
+    if (g->scheme.precision == SENSEI_DF64) return 3;
     return in_f32 ? 2 : 1;
 }
 
@@ -493,6 +495,10 @@ sensei_status stencil_launch(sensei_grid *g, const StencilCall &c, cudaStream_t 
         BatchParams<double> p;
         fill_params(p, g, c);
         CUDA_TRY(launch_stencil_f64(p, g->scheme.limiter, g->plan.two_d, grid, s));
+    } else if (kind == 3) {
+        BatchParams<df64> p;
+        fill_params(p, g, c);
+        CUDA_TRY(launch_stencil_df64(p, g->scheme.limiter, g->plan.two_d, grid, s));
     } else {
         BatchParams<float> p;
         fill_params(p, g, c);
@@ -570,7 +576,8 @@ sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, doub
         CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
         CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, local ? 1 : 0,
                            cfl, grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms),
-                           grid->scheme.precision != SENSEI_FP64, viscous_dt_factor(grid), s));
+                           grid->scheme.precision == SENSEI_FP32_FLUX || grid->scheme.precision == SENSEI_FP32_STORE,
+                           viscous_dt_factor(grid), s));
         grid->kernel_launches++;
         dt_src = (const double *)grid->dt_bits;
         dt_scale = cfl;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "sensei.h"
+#include "df64.cuh"
 
 namespace sensei {
 
@@ -178,6 +179,9 @@ cudaError_t launch_stencil_f64(const BatchParams<double> &p, int limiter, bool t
 cudaError_t launch_stencil_f32(const BatchParams<float> &p, int limiter, bool two_d, int grid, cudaStream_t s);
 // FP32 arithmetic on an FP32 stage state
 cudaError_t launch_stencil_f32s(const BatchParams<float> &p, int limiter, bool two_d, int grid, cudaStream_t s);
+// double-float arithmetic on an FP64 state
+cudaError_t launch_stencil_df64(const BatchParams<df64> &p, int limiter, bool two_d, int grid, cudaStream_t s);
+int stencil_ctas_per_sm_df64(int limiter, bool two_d);
 // resident CTAs per SM of a stencil variant (0 on error); precision_kind
 // 0 = FP64, 1 = FP32 arithmetic on an FP64 state, 2 = on an FP32 state
 int stencil_ctas_per_sm(int precision_kind, int limiter, bool two_d);

@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "blocks.cuh"
+#include "df64.cuh"
 
 // CTAs per SM the register allocation must allow: 2 for FP64 arithmetic
 // (the FP64 pipe is the bound; more warps cover its dependent latency), 3
@@ -118,6 +119,14 @@ template <>
 __device__ __forceinline__ double rsqrt1_t<double>(double x) { return rsqrt_nr<1>(x); }
 template <>
 __device__ __forceinline__ float rsqrt1_t<float>(float x) { return rsqrt_approx(x); }
+// double-float: one Newton step from the single-precision approximation
+// (23 -> about 46 bits) in both cases
+template <>
+__device__ __forceinline__ df64 rcp_t<df64, 1>(df64 x) { return rcp_df(x); }
+template <>
+__device__ __forceinline__ df64 rcp_t<df64, 2>(df64 x) { return rcp_df(x); }
+template <>
+__device__ __forceinline__ df64 rsqrt1_t<df64>(df64 x) { return rsqrt_df(x); }
 
 // x > 0 (nonzero, not NaN) and the sign of x, from the bit pattern (integer
 // pipe, keeps compares off the FP64 pipe)
@@ -139,6 +148,12 @@ __device__ __forceinline__ bool positive_finite(float x)
 // a < b for a, b >= 0 (or NaN, which compares false) by the bit patterns
 __device__ __forceinline__ bool lt_nonneg(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
 __device__ __forceinline__ bool lt_nonneg(float a, float b) { return __float_as_int(a) < __float_as_int(b); }
+// the double-float forms: the sign is the high part's; magnitudes compare
+// the high parts, then the (sign-adjusted) low parts
+__device__ __forceinline__ bool positive(df64 x) { return positive(x.hi); }
+__device__ __forceinline__ bool positive_finite(df64 x) { return positive_finite(x.hi); }
+__device__ __forceinline__ bool same_sign(df64 a, df64 b) { return same_sign(a.hi, b.hi); }
+__device__ __forceinline__ bool lt_nonneg(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 // |a| <= |b| by the bit patterns of the magnitudes
 __device__ __forceinline__ bool abs_le(double a, double b)
 {
@@ -147,6 +162,13 @@ __device__ __forceinline__ bool abs_le(double a, double b)
 __device__ __forceinline__ bool abs_le(float a, float b)
 {
     return (__float_as_int(a) & 0x7fffffff) <= (__float_as_int(b) & 0x7fffffff);
+}
+__device__ __forceinline__ bool abs_le(df64 a, df64 b)
+{
+    const float ah = fabsf(a.hi), bh = fabsf(b.hi);
+    if (ah != bh) return ah < bh;
+    const float al = a.hi < 0.0f ? -a.lo : a.lo, bl = b.hi < 0.0f ? -b.lo : b.lo;
+    return al <= bl;
 }
 
 // FP64 <-> FP32 conversions on the integer pipe, from the IEEE-754 binary64
@@ -193,6 +215,18 @@ template <>
 __device__ __forceinline__ float cvt<float, double>(double x) { return to_f32(x); }
 template <>
 __device__ __forceinline__ double cvt<double, float>(float x) { return to_f64(x); }
+// double <-> double-float: the split rounds on the integer pipe; the
+// remainder takes one FP64 subtraction
+template <>
+__device__ __forceinline__ df64 cvt<df64, double>(double x)
+{
+    const float h = to_f32(x);
+    return df64(h, to_f32(x - to_f64(h)));
+}
+template <>
+__device__ __forceinline__ double cvt<double, df64>(df64 x) { return to_f64(x.hi) + to_f64(x.lo); }
+template <>
+__device__ __forceinline__ df64 cvt<df64, df64>(df64 x) { return x; }
 
 // conserved -> primitive; true if rho > 0, p > 0 and both finite
 template <typename R>
@@ -368,10 +402,7 @@ __device__ __forceinline__ void to_recon(const R q[NV], R gm1, int cons, bool in
 }
 
 // Face metrics of one block in the arithmetic type R.
-template <typename R>
-__device__ __forceinline__ const R *face_metric_base(const BlockDev &B);
-template <>
-__device__ __forceinline__ const double *face_metric_base<double>(const BlockDev &B) { return B.fn; }
+
 
 // The output buffer of a stage for block n: FP64 (the caller's U or an FP64
 // stage state) or FP32 (an FP32 stage state).
@@ -507,7 +538,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
         const bool col_valid = ci < B.ni && cj < B.nj;
         const StateLayout L = B.L;
         const MetricLayout ml = B.ml;
-        const R *fm = face_metric_base<R>(B);   // [family*4 + q][mvolume]
+        const double *fm = B.fn;   // FP64 face metrics [family*4 + q][mvolume]
         const TS *in = (p.in_slot == SLOT_X0 || p.in_slot == SLOT_X1)
                            ? reinterpret_cast<const TS *>(slot32(B, p.in_slot))
                            : reinterpret_cast<const TS *>(slot64(B, p.user[b], p.in_slot));
@@ -549,9 +580,10 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                 face_states<R, LIM>(Wm1[v], Wc[v], W1[v], c1, c2, half_eps, Pp[v], Rk[v]);
             }
             const long long fk = (long long)k0 * ml.mplane + (long long)min(cj, B.nj - 1) * ml.mpitch + min(ci, B.ni - 1);
-            const R *f2 = fm + 8 * ml.mvolume;
-            face_flux(Lk, Rk, f2[fk], f2[ml.mvolume + fk], f2[2 * ml.mvolume + fk], f2[3 * ml.mvolume + fk], gm1, kg,
-                      p.fix, cons, Fkm);
+            const double *f2 = fm + 8 * ml.mvolume;
+            face_flux(Lk, Rk, cvt<R, double>(f2[fk]), cvt<R, double>(f2[ml.mvolume + fk]),
+                      cvt<R, double>(f2[2 * ml.mvolume + fk]), cvt<R, double>(f2[3 * ml.mvolume + fk]), gm1, kg, p.fix,
+                      cons, Fkm);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 sK[v * NTHREADS + t] = W1[v];
@@ -671,12 +703,12 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                 bool valid = fam == 0 ? (fi <= B.ni && fj < B.nj) : (fi < B.ni && fj <= B.nj);
                 R nx = R(1), ny = R(0), nz = R(0), A = R(0);
                 if (valid) {
-                    const R *fb = fm + (long long)(fam * 4) * ml.mvolume;
+                    const double *fb = fm + (long long)(fam * 4) * ml.mvolume;
                     const long long m = kpl + (long long)fj * ml.mpitch + fi;
-                    nx = fb[m];
-                    ny = fb[ml.mvolume + m];
-                    nz = fb[2 * ml.mvolume + m];
-                    A = fb[3 * ml.mvolume + m];
+                    nx = cvt<R, double>(fb[m]);
+                    ny = cvt<R, double>(fb[ml.mvolume + m]);
+                    nz = cvt<R, double>(fb[2 * ml.mvolume + m]);
+                    A = cvt<R, double>(fb[3 * ml.mvolume + m]);
                 }
                 face_flux(Lf, Rf, nx, ny, nz, A, gm1, kg, p.fix, cons, F);
                 const int vstride = fam == 0 ? FIV : FJV;
@@ -694,9 +726,10 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                                         sK[((kb ^ 1) * NV + v) * NTHREADS + t], c1, c2, half_eps, Ppn[v], Rk[v]);
                 const long long fk = (long long)(k + 1) * ml.mplane + (long long)min(cj, B.nj - 1) * ml.mpitch +
                                      min(ci, B.ni - 1);
-                const R *f2 = fm + 8 * ml.mvolume;
-                face_flux(Pp, Rk, f2[fk], f2[ml.mvolume + fk], f2[2 * ml.mvolume + fk], f2[3 * ml.mvolume + fk], gm1,
-                          kg, p.fix, cons, Fkp);
+                const double *f2 = fm + 8 * ml.mvolume;
+                face_flux(Pp, Rk, cvt<R, double>(f2[fk]), cvt<R, double>(f2[ml.mvolume + fk]),
+                          cvt<R, double>(f2[2 * ml.mvolume + fk]), cvt<R, double>(f2[3 * ml.mvolume + fk]), gm1, kg,
+                          p.fix, cons, Fkp);
             }
             __syncthreads();
 

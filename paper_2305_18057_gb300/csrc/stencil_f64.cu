@@ -19,6 +19,7 @@ int stencil_ctas_per_sm(int precision_kind, int limiter, bool two_d)
         const int b = stencil_ctas_per_sm_f64_part(limiter, two_d);
         return a < b ? a : b;
     }
+    if (precision_kind == 3) return stencil_ctas_per_sm_df64(limiter, two_d);
     return stencil_ctas_per_sm_f32(precision_kind, limiter, two_d);
 }
 }  // namespace sensei

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsensei.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_STATE = range(7)
-FP64, FP32_FLUX, FP32_STORE = 0, 1, 2
+FP64, FP32_FLUX, FP32_STORE, DF64 = 0, 1, 2, 3
 BC_PERIODIC, BC_INFLOW, BC_EXTRAPOLATE, BC_SLIP_WALL, BC_INTERFACE = range(5)
 RK2_SSP, RK3_SSP, RK4_SSP2 = range(3)
 LIM_NONE, LIM_MINMOD, LIM_VANLEER = range(3)
