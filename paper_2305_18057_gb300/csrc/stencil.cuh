@@ -351,18 +351,24 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
 
 // The face flux from the two reconstructed states (primitive, or conserved
 // when p.cons is set).
+// One inlined copy of the Roe flux per call site (the branch only converts
+// the states).
 template <typename R>
 __device__ __forceinline__ void face_flux(R L[NV], R Rt[NV], R nx, R ny, R nz, R A, R gm1, R kg, R fix, int cons,
                                           R F[NV])
 {
+    R wl[NV], wr[NV];
     if (cons) {
-        R wl[NV], wr[NV];
         to_prim(L, gm1, wl);
         to_prim(Rt, gm1, wr);
-        roe_flux(wl, wr, nx, ny, nz, A, gm1, kg, fix, F);
     } else {
-        roe_flux(L, Rt, nx, ny, nz, A, gm1, kg, fix, F);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            wl[v] = L[v];
+            wr[v] = Rt[v];
+        }
     }
+    roe_flux(wl, wr, nx, ny, nz, A, gm1, kg, fix, F);
 }
 
 // Loads a cell of the stage input (storage type TS) as the arithmetic type R.
