@@ -562,42 +562,35 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
         // registers until the plane's P0 puts it in sW), planes k+1 and k+2
         // in sK[kb] and sK[kb ^ 1] (each thread its own entries), the
         // plus-side k-state of the centre plane and the flux of its lower
-        // k-face in registers
+        // k-face in registers.  The window opens one plane early: the
+        // iteration k = k0 - 1 only forms the flux of face k0 - 1/2, through
+        // the same face loop as every other face.
         R Wc[NV], Pp[NV], Fkm[NV];
         int kb = 0;
         if (!TWO_D) {
             R q[NV];
-            R Wm2[NV], Wm1[NV], W1[NV], W2[NV];
+            R Wm2[NV], W0[NV], W1[NV];
             ld.raw(ci, cj, k0 - 2, q);
             to_recon(q, gm1, cons, false, p.err, Wm2);
             ld.raw(ci, cj, k0 - 1, q);
-            to_recon(q, gm1, cons, false, p.err, Wm1);
+            to_recon(q, gm1, cons, false, p.err, Wc);
             ld.raw(ci, cj, k0, q);
-            to_recon(q, gm1, cons, col_valid, p.err, Wc);
+            to_recon(q, gm1, cons, col_valid, p.err, W0);
             ld.raw(ci, cj, k0 + 1, q);
             to_recon(q, gm1, cons, col_valid && k0 + 1 < B.nk, p.err, W1);
-            ld.raw(ci, cj, k0 + 2, q);
-            to_recon(q, gm1, cons, col_valid && k0 + 2 < B.nk, p.err, W2);
-            // face k0-1/2: left state from plane k0-1, right state from plane k0
-            R Lk[NV], Rk[NV], dummy;
+            // plus-side state of plane k0 - 1 (left state of face k0 - 1/2)
+            R dummy;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                face_states<R, LIM>(Wm2[v], Wm1[v], Wc[v], c1, c2, half_eps, Lk[v], dummy);
-                face_states<R, LIM>(Wm1[v], Wc[v], W1[v], c1, c2, half_eps, Pp[v], Rk[v]);
-            }
-            const long long fk = (long long)k0 * ml.mplane + (long long)min(cj, B.nj - 1) * ml.mpitch + min(ci, B.ni - 1);
-            const double *f2 = fm + 8 * ml.mvolume;
-            face_flux(Lk, Rk, cvt<R, double>(f2[fk]), cvt<R, double>(f2[ml.mvolume + fk]),
-                      cvt<R, double>(f2[2 * ml.mvolume + fk]), cvt<R, double>(f2[3 * ml.mvolume + fk]), gm1, kg, p.fix,
-                      cons, Fkm);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                sK[v * NTHREADS + t] = W1[v];
-                sK[(NV + v) * NTHREADS + t] = W2[v];
+                face_states<R, LIM>(Wm2[v], Wc[v], W0[v], c1, c2, half_eps, Pp[v], dummy);
+                sK[v * NTHREADS + t] = W0[v];
+                sK[(NV + v) * NTHREADS + t] = W1[v];
+                Fkm[v] = R(0);
             }
         }
 
-        for (int k = k0; k < k1; ++k) {
+        for (int k = TWO_D ? k0 : k0 - 1; k < k1; ++k) {
+            const bool warm = !TWO_D && k < k0;
             // ---- P0: the centre plane with its halo into shared memory
             R pre[NV];
             if (!TWO_D) {
@@ -605,7 +598,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
 #pragma unroll
                 for (int v = 0; v < NV; ++v) W_at(v, tj, ti) = Wc[v];
                 // halo ring: 2 columns each side of the TJ rows, 2 rows each side of the TI columns
-                for (int e = t; e < 4 * TJ + 4 * TI; e += NTHREADS) {
+                for (int e = warm ? NTHREADS : t; e < 4 * TJ + 4 * TI; e += NTHREADS) {
                     int r, c;
                     if (e < 4 * TJ) {
                         r = e >> 2;
@@ -644,7 +637,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
 
             // ---- P1: face states, i direction (cells -1..TI of every row)
             //      and j direction (rows -1..TJ of every column)
-            for (int e = t; e < TJ * (TI + 2) + (TJ + 2) * TI; e += NTHREADS) {
+            for (int e = warm ? TJ * (TI + 2) + (TJ + 2) * TI : t; e < TJ * (TI + 2) + (TJ + 2) * TI; e += NTHREADS) {
                 // the centre cell in sW, the stride to its neighbours along
                 // the direction, and where its two face states go
                 int wc, ws;
@@ -676,14 +669,43 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
             }
             __syncthreads();
 
-            // ---- P2: Roe flux of every i-face and j-face of the tile, once each
+            // ---- P2: Roe flux of every face of the tile, once each, through
+            //      one copy of the flux code: first each thread's own face
+            //      k+1/2 (left = plus state of plane k, right = minus state
+            //      of plane k+1), then the i-faces and j-faces from the
+            //      shared face states
             const long long kpl = (long long)k * ml.mplane;
-            for (int e = t; e < TJ * (TI + 1) + (TJ + 1) * TI; e += NTHREADS) {
+            constexpr int NKF = TWO_D ? 0 : NTHREADS;
+            constexpr int NIJ = TJ * (TI + 1) + (TJ + 1) * TI;
+            R Fkp[NV], Ppn[NV], Rk[NV];
+            if (!TWO_D) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+                    face_states<R, LIM>(W_at(v, tj, ti), sK[(kb * NV + v) * NTHREADS + t],
+                                        sK[((kb ^ 1) * NV + v) * NTHREADS + t], c1, c2, half_eps, Ppn[v], Rk[v]);
+            }
+#pragma unroll 1
+            for (int e = t; e < (warm ? NKF : NKF + NIJ); e += NTHREADS) {
                 R Lf[NV], Rf[NV], F[NV];
                 int fam, fi, fj;
-                R *dst;
-                if (e < TJ * (TI + 1)) {
-                    int r = e / (TI + 1), c = e % (TI + 1);   // face between cells c-1 and c of row r
+                long long fplane;
+                R *dst = nullptr;
+                int vstride = 0;
+                bool valid;
+                if (e < NKF) {   // e == t
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        Lf[v] = Pp[v];
+                        Rf[v] = Rk[v];
+                    }
+                    fam = 2;
+                    fi = min(ci, B.ni - 1);
+                    fj = min(cj, B.nj - 1);
+                    fplane = (long long)(k + 1) * ml.mplane;
+                    valid = true;
+                } else if (e < NKF + TJ * (TI + 1)) {
+                    const int f = e - NKF;
+                    const int r = f / (TI + 1), c = f % (TI + 1);   // face between cells c-1 and c of row r
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         Lf[v] = sPi[v * PIV + r * PIP + c];
@@ -692,10 +714,13 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                     fam = 0;
                     fi = i0 + c;
                     fj = j0 + r;
+                    fplane = kpl;
                     dst = sFi + r * FIP + c;
+                    vstride = FIV;
+                    valid = fi <= B.ni && fj < B.nj;
                 } else {
-                    int e2 = e - TJ * (TI + 1);
-                    int r = e2 / TI, c = e2 % TI;              // face between rows r-1 and r of column c
+                    const int f = e - NKF - TJ * (TI + 1);
+                    const int r = f / TI, c = f % TI;              // face between rows r-1 and r of column c
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         Lf[v] = sPj[v * PJV + r * PJP + c];
@@ -704,43 +729,33 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                     fam = 1;
                     fi = i0 + c;
                     fj = j0 + r;
+                    fplane = kpl;
                     dst = sFj + r * FJP + c;
+                    vstride = FJV;
+                    valid = fi < B.ni && fj <= B.nj;
                 }
-                bool valid = fam == 0 ? (fi <= B.ni && fj < B.nj) : (fi < B.ni && fj <= B.nj);
                 R nx = R(1), ny = R(0), nz = R(0), A = R(0);
                 if (valid) {
                     const double *fb = fm + (long long)(fam * 4) * ml.mvolume;
-                    const long long m = kpl + (long long)fj * ml.mpitch + fi;
+                    const long long m = fplane + (long long)fj * ml.mpitch + fi;
                     nx = cvt<R, double>(fb[m]);
                     ny = cvt<R, double>(fb[ml.mvolume + m]);
                     nz = cvt<R, double>(fb[2 * ml.mvolume + m]);
                     A = cvt<R, double>(fb[3 * ml.mvolume + m]);
                 }
                 face_flux(Lf, Rf, nx, ny, nz, A, gm1, kg, p.fix, cons, F);
-                const int vstride = fam == 0 ? FIV : FJV;
+                if (e < NKF) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) dst[v * vstride] = F[v];
-            }
-            R Fkp[NV], Ppn[NV];
-            if (!TWO_D) {
-                // face k+1/2 of the own column: left = plus state of plane k,
-                // right = minus state of plane k+1
-                R Rk[NV];
+                    for (int v = 0; v < NV; ++v) Fkp[v] = F[v];
+                } else {
 #pragma unroll
-                for (int v = 0; v < NV; ++v)
-                    face_states<R, LIM>(W_at(v, tj, ti), sK[(kb * NV + v) * NTHREADS + t],
-                                        sK[((kb ^ 1) * NV + v) * NTHREADS + t], c1, c2, half_eps, Ppn[v], Rk[v]);
-                const long long fk = (long long)(k + 1) * ml.mplane + (long long)min(cj, B.nj - 1) * ml.mpitch +
-                                     min(ci, B.ni - 1);
-                const double *f2 = fm + 8 * ml.mvolume;
-                face_flux(Pp, Rk, cvt<R, double>(f2[fk]), cvt<R, double>(f2[ml.mvolume + fk]),
-                          cvt<R, double>(f2[2 * ml.mvolume + fk]), cvt<R, double>(f2[3 * ml.mvolume + fk]), gm1, kg,
-                          p.fix, cons, Fkp);
+                    for (int v = 0; v < NV; ++v) dst[v * vstride] = F[v];
+                }
             }
             __syncthreads();
 
             // ---- P3: residual, update, ghost push, norms
-            if (col_valid) {
+            if (col_valid && !warm) {
                 const long long cell = L.off + (long long)k * L.sk + (long long)cj * L.sj + ci;
                 const long long mc = kpl + (long long)cj * ml.mpitch + ci;
                 R rres[NV];
