@@ -56,6 +56,17 @@ WORKLOADS = {
 ROE_FLOPS = 157
 STATE_FLOPS = {"none": 25, "minmod": 30, "vanleer": 45}
 
+# The same step as the oracle states it, counted by its op-counting build
+# (oracle/opcount.cpp): operations per cell and RK stage over one SSPRK3 step
+# (dt, three residuals and updates, norms) of the periodic 3D workload at
+# 24^3, van Leer.  The plain oracle recomputes primitives for every face
+# stencil, takes the limiter in its ratio form (a division per ratio) and
+# normalises each face vector per call, so it performs about twice the
+# kernel's operations; the kernel's own count above is the one the roofline
+# uses (tests/test_oracle_opcount.py re-counts these numbers).
+ORACLE_OPS_PER_CELL_STAGE = {"add": 682.894, "mul": 695.093, "div": 231.769, "sqrt": 10.708,
+                             "cmp": 74.875, "abs": 117.771}
+
 
 def alg_flops_per_cell(limiter, two_d, alpha_nonzero, first_stage):
     nd = 2 if two_d else 3
@@ -416,6 +427,7 @@ def main():
             "kernel": "stencil_kernel<double,double> (fused MUSCL + Roe + residual + RK stage)",
             "peak_source": "derived FP64 vector peak: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
             "alg_flops_per_launch": flops, "kernel_ms_per_launch": per_launch_ms,
+            "oracle_ops_per_cell_stage": ORACLE_OPS_PER_CELL_STAGE,
             "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_gbs / peaks["hbm_gbs"],
                     "peak_source": peak_src, "alg_bytes_per_launch": byts},
         }

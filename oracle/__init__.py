@@ -26,6 +26,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "sensei_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "libsensei_oracle.so")
+# the same source compiled with a double that counts its operations
+OPCOUNT_SRC = os.path.join(HERE, "opcount.cpp")
+OPCOUNT_LIB = os.path.join(BUILD_DIR, "libsensei_oracle_opcount.so")
 
 # boundary-condition, limiter and Runge-Kutta codes of the oracle
 BC_PERIODIC, BC_INFLOW, BC_EXTRAPOLATE, BC_SLIP_WALL, BC_INTERFACE = 0, 1, 2, 3, 4
@@ -34,30 +37,35 @@ RK2_SSP, RK3_SSP, RK4_SSP2 = 0, 1, 2
 NV, NG = 5, 2
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 _dp = C.POINTER(C.c_double)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/libsensei_oracle.so``."""
+def build(force: bool = False, counting: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/libsensei_oracle.so`` (or,
+    with ``counting``, its op-counting build ``libsensei_oracle_opcount.so``)."""
     os.makedirs(BUILD_DIR, exist_ok=True)
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
-        return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp, SRC, "-lm"]
+    out, srcs = (OPCOUNT_LIB, [OPCOUNT_SRC, SRC]) if counting else (LIB, [SRC])
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= max(os.path.getmtime(f) for f in srcs)):
+        return out
+    tmp = out + f".{os.getpid()}.tmp"
+    if counting:
+        cmd = ["g++", "-O2", "-std=c++17", "-fpermissive", "-w", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, OPCOUNT_SRC, "-lm"]
+    else:
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+def lib(counting: bool = False):
     with _lock:
-        if _lib is None:
-            path = build()
+        if counting not in _libs:
+            path = build(counting=counting)
             L = C.CDLL(path)
             L.ora_create.restype = C.c_void_p
             L.ora_create.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(_dp), C.c_double,
@@ -86,8 +94,28 @@ def lib():
             L.ora_psi.argtypes = [C.c_int, C.c_double]
             L.ora_cons_to_prim.argtypes = [C.c_double, _dp, _dp]
             L.ora_prim_to_cons.argtypes = [C.c_double, _dp, _dp]
-            _lib = L
-    return _lib
+            if counting:
+                L.ora_opcount_reset.argtypes = []
+                L.ora_opcount_get.argtypes = [C.POINTER(C.c_ulonglong)]
+            _libs[counting] = L
+    return _libs[counting]
+
+
+OPCOUNT_KINDS = ("add", "mul", "div", "sqrt", "cmp", "abs", "neg")
+
+
+def opcount_reset():
+    """Zero the operation counters of the op-counting build."""
+    lib(counting=True).ora_opcount_reset()
+
+
+def opcount_get():
+    """Operations counted since the last reset: additions/subtractions,
+    multiplications, divisions, square roots, comparisons, absolute values and
+    min/max, negations."""
+    out = (C.c_ulonglong * len(OPCOUNT_KINDS))()
+    lib(counting=True).ora_opcount_get(out)
+    return dict(zip(OPCOUNT_KINDS, (int(v) for v in out)))
 
 
 def _ptr(a: np.ndarray):
@@ -172,22 +200,23 @@ class OracleGrid:
     """Multiblock structured grid held by the oracle (metrics computed in C)."""
 
     def __init__(self, dims, nodes, gamma=1.4, limiter=LIM_VANLEER, kappa=1.0 / 3.0, eps=1.0,
-                 recon_conserved=False, fix=0.1, mu=0.0, prandtl=0.72):
+                 recon_conserved=False, fix=0.1, mu=0.0, prandtl=0.72, counting=False):
+        self._L = lib(counting)
         self.dims = [tuple(int(v) for v in d) for d in dims]
         self.nodes = [np.ascontiguousarray(x, dtype=np.float64) for x in nodes]
         for (ni, nj, nk), X in zip(self.dims, self.nodes):
             assert X.shape == (3, nk + 1, nj + 1, ni + 1), (X.shape, (ni, nj, nk))
         flat = (C.c_int * (3 * len(self.dims)))(*[v for d in self.dims for v in d])
-        self._h = lib().ora_create(len(self.dims), flat, _ptrs(self.nodes), gamma, limiter, kappa,
+        self._h = self._L.ora_create(len(self.dims), flat, _ptrs(self.nodes), gamma, limiter, kappa,
                                    eps, int(recon_conserved), fix)
-        lib().ora_set_viscosity(self._h, mu, prandtl)
+        self._L.ora_set_viscosity(self._h, mu, prandtl)
         self.gamma = gamma
         self.mu, self.prandtl = mu, prandtl
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().ora_destroy(h)
+            self._L.ora_destroy(h)
             self._h = None
 
     @property
@@ -211,7 +240,7 @@ class OracleGrid:
 
     def set_bc(self, b, face, bc_type, prim=None, nbr=-1, nbr_face=-1):
         p = _vec(prim, 5) if prim is not None else None
-        rc = lib().ora_set_bc(self._h, b, face, bc_type, _ptr(p) if p is not None else _dp(), nbr, nbr_face)
+        rc = self._L.ora_set_bc(self._h, b, face, bc_type, _ptr(p) if p is not None else _dp(), nbr, nbr_face)
         if rc != 0:
             raise ValueError(f"oracle rejected boundary condition (code {rc})")
 
@@ -221,11 +250,11 @@ class OracleGrid:
         Sj = np.zeros((3, nk, nj + 1, ni))
         Sk = np.zeros((3, nk + 1, nj, ni))
         vol = np.zeros((nk, nj, ni))
-        lib().ora_get_metrics(self._h, b, _ptr(Si), _ptr(Sj), _ptr(Sk), _ptr(vol))
+        self._L.ora_get_metrics(self._h, b, _ptr(Si), _ptr(Sj), _ptr(Sk), _ptr(vol))
         return Si, Sj, Sk, vol
 
     def fill_ghosts(self, Us):
-        lib().ora_fill_ghosts(self._h, _ptrs(Us))
+        self._L.ora_fill_ghosts(self._h, _ptrs(Us))
 
     def residual(self, Us, src=None, fill=True):
         """R_h of Eq. residual for every block; fills the ghost layers first."""
@@ -233,17 +262,17 @@ class OracleGrid:
             self.fill_ghosts(Us)
         Rs = [np.zeros((NV,) + tuple(reversed(d))) for d in self.dims]
         srcp = _ptrs(src) if src is not None else None
-        lib().ora_residual(self._h, _ptrs(Us), _ptrs(Rs), srcp)
+        self._L.ora_residual(self._h, _ptrs(Us), _ptrs(Rs), srcp)
         return Rs
 
     def dt_min(self, Us, fill=True):
         if fill:
             self.fill_ghosts(Us)
-        return lib().ora_dt_min(self._h, _ptrs(Us))
+        return self._L.ora_dt_min(self._h, _ptrs(Us))
 
     def norms(self, Rs, Us):
         out = np.zeros(15)
-        lib().ora_norms(self._h, _ptrs(Rs), _ptrs(Us), _ptr(out))
+        self._L.ora_norms(self._h, _ptrs(Rs), _ptrs(Us), _ptr(out))
         return out[:5].copy(), out[5:10].copy(), out[10:].copy()
 
     def rk_step_local(self, Us, rk=RK3_SSP, cfl=0.5, src=None):
@@ -251,12 +280,12 @@ class OracleGrid:
         (smallest dt, norms)."""
         out = np.zeros(15)
         srcp = _ptrs(src) if src is not None else None
-        dt_min = lib().ora_rk_step_local(self._h, _ptrs(Us), srcp, rk, cfl, _ptr(out))
+        dt_min = self._L.ora_rk_step_local(self._h, _ptrs(Us), srcp, rk, cfl, _ptr(out))
         return dt_min, (out[:5].copy(), out[5:10].copy(), out[10:].copy())
 
     def rk_step(self, Us, rk=RK3_SSP, cfl=0.5, dt=0.0, src=None):
         """One Runge-Kutta step in place; returns (dt_used, (l2, linf, cons))."""
         out = np.zeros(15)
         srcp = _ptrs(src) if src is not None else None
-        dt_used = lib().ora_rk_step(self._h, _ptrs(Us), srcp, rk, cfl, dt, _ptr(out))
+        dt_used = self._L.ora_rk_step(self._h, _ptrs(Us), srcp, rk, cfl, dt, _ptr(out))
         return dt_used, (out[:5].copy(), out[5:10].copy(), out[10:].copy())
