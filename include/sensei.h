@@ -72,7 +72,8 @@ typedef enum {
     SENSEI_DF64 = 3         /* FP64 state; reconstruction and flux in double-float arithmetic
                              * (pairs of FP32 numbers, about 48 significant bits, computed on
                              * the FP32 pipe); not in the paper: an FP64-class alternative for
-                             * GPUs whose FP64 pipe is narrow */
+                             * GPUs whose FP64 pipe is narrow.  The workspace then also holds
+                             * the face metrics split into float pairs (96 B per cell) */
 } sensei_precision;
 
 /* Ghost-cell rules, 2 ghost layers per boundary face. */

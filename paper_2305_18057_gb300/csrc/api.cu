@@ -68,7 +68,7 @@ struct HostBlock {
 // sensei_workspace_size and sensei_create_grid.
 struct Plan {
     std::vector<HostBlock> blocks;
-    std::vector<size_t> off_fn, off_rec32, off_vol, off_ivol, off_sbar, off_sbar32, off_dtv, off_stage, off_wv,
+    std::vector<size_t> off_fn, off_fdf, off_rec32, off_vol, off_ivol, off_sbar, off_sbar32, off_dtv, off_stage, off_wv,
         off_rvis, off_fvis, off_gvis;
     size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0;
     size_t bytes = 0;
@@ -148,7 +148,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     if (st != SENSEI_OK) return st;
     size_t cur = 0;
     P.blocks.resize(nblocks);
-    for (auto *v : {&P.off_fn, &P.off_rec32, &P.off_vol, &P.off_ivol, &P.off_sbar, &P.off_sbar32, &P.off_dtv,
+    for (auto *v : {&P.off_fn, &P.off_fdf, &P.off_rec32, &P.off_vol, &P.off_ivol, &P.off_sbar, &P.off_sbar32, &P.off_dtv,
                     &P.off_wv, &P.off_rvis, &P.off_fvis, &P.off_gvis,
                     &P.off_stage})
         v->resize(nblocks);
@@ -193,6 +193,8 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         P.ncells += (long long)d.ni * d.nj * d.nk;
         const size_t mv = (size_t)B.ml.mvolume;
         P.off_fn[b] = take(cur, 12 * mv * sizeof(double));
+        // double-float: the face metrics split once into float pairs
+        P.off_fdf[b] = scheme->precision == SENSEI_DF64 ? take(cur, 12 * mv * 2 * sizeof(float)) : 0;
         P.off_rec32[b] =
             f32 ? take(cur, (size_t)B.tiles_i * B.tiles_j * d.nk * REC * sizeof(float)) : 0;
         P.off_vol[b] = take(cur, mv * sizeof(double));
@@ -760,6 +762,7 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
         BlockDev &B = g->plan.blocks[b].dev;
         const size_t mv = (size_t)B.ml.mvolume;
         B.fn = (const double *)(g->ws + P.off_fn[b]);
+        B.fdf = P.off_fdf[b] ? (const float2 *)(g->ws + P.off_fdf[b]) : nullptr;
         B.rec32 = P.off_rec32[b] ? (const float *)(g->ws + P.off_rec32[b]) : nullptr;
         B.vol = (const double *)(g->ws + P.off_vol[b]);
         B.ivol = (const double *)(g->ws + P.off_ivol[b]);
@@ -791,6 +794,7 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
         mo.vol32 = (float *)B.vol32;
         cudaError_t e = launch_metrics(B.ni, B.nj, B.nk, nodes[b], mo, B.ml, s);
         if (e == cudaSuccess) e = launch_pack_records(B, s);
+        if (e == cudaSuccess) e = launch_split_df64(B, s);
         if (e != cudaSuccess) {
             delete g;
             return fail(SENSEI_ERR_CUDA, "metrics kernel: %s", cudaGetErrorString(e));

@@ -23,7 +23,7 @@ using ::fma;
 
 struct df64 {
     float hi, lo;
-    __host__ __device__ df64() = default;
+    df64() = default;
     // exact small constants (0.5, 1, 2, 2.5, 4 ...) and FP32 values
     __host__ __device__ constexpr explicit df64(float h) : hi(h), lo(0.0f) {}
     __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}

@@ -314,6 +314,27 @@ cudaError_t launch_pack_records(const BlockDev &B, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// x = hi + lo with hi the float nearest to x and lo the float nearest to the
+// remainder (exact in double): the double-float form of the face metrics
+__global__ void split_df64_kernel(const double *__restrict__ x, float2 *__restrict__ out, long long n)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const double v = x[e];
+        const float hi = __double2float_rn(v);
+        out[e] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+}
+
+cudaError_t launch_split_df64(const BlockDev &B, cudaStream_t s)
+{
+    if (!B.fdf) return cudaSuccess;
+    const long long n = 12LL * B.ml.mvolume;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    split_df64_kernel<<<(unsigned)blocks, 256, 0, s>>>(B.fn, const_cast<float2 *>(B.fdf), n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_edges(const BCBatch &p, int max_units, cudaStream_t s)
 {
     const dim3 grid((unsigned)std::max(1, std::min((max_units + 255) / 256, 64)), (unsigned)p.nblocks);

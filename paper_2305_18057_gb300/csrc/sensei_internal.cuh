@@ -79,6 +79,7 @@ struct BlockDev {
     StateLayout L;
     MetricLayout ml;
     const double *fn;       // face metrics: 12 arrays of mvolume, index (family*4 + q)
+    const float2 *fdf;      // double-float grids: fn as (hi, lo) float pairs, same index (else null)
     const float *rec32;     // FP32 face-metric records of the FP32 stencil (null in FP64 mode)
     const double *vol, *ivol;
     const double *sbar;     // spectral metrics: 12 arrays of mvolume, index (direction*4 + q)
@@ -173,6 +174,7 @@ cudaError_t launch_bc(const BCBatch &p, cudaStream_t s);
 cudaError_t launch_edges(const BCBatch &p, int max_units, cudaStream_t s);
 // pack block B's FP64 face metrics and 1/|Omega| into its FP32 records B.rec32
 cudaError_t launch_pack_records(const BlockDev &B, cudaStream_t s);
+cudaError_t launch_split_df64(const BlockDev &B, cudaStream_t s);
 // FP64 arithmetic on an FP64 state
 cudaError_t launch_stencil_f64(const BatchParams<double> &p, int limiter, bool two_d, int grid, cudaStream_t s);
 // FP32 arithmetic on an FP64 state (FP32 flux; first FP32-storage stage; residuals)

@@ -395,6 +395,21 @@ struct CellLoader {
     }
 };
 
+// One face-metric value (index into the 12 arrays of mvolume) in the
+// arithmetic type: converted from FP64, or, for double-float, read from the
+// copy split once at grid set-up.
+template <typename R>
+__device__ __forceinline__ R face_metric(const double *fm, const float2 *, long long idx)
+{
+    return cvt<R, double>(fm[idx]);
+}
+template <>
+__device__ __forceinline__ df64 face_metric<df64>(const double *, const float2 *fdm, long long idx)
+{
+    const float2 v = __ldg(fdm + idx);
+    return df64(v.x, v.y);
+}
+
 // Convert a loaded cell to the reconstructed variables; flag non-physical
 // interior cells.
 template <typename R>
@@ -544,7 +559,8 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
         const bool col_valid = ci < B.ni && cj < B.nj;
         const StateLayout L = B.L;
         const MetricLayout ml = B.ml;
-        const double *fm = B.fn;   // FP64 face metrics [family*4 + q][mvolume]
+        const double *fm = B.fn;     // FP64 face metrics [family*4 + q][mvolume]
+        const float2 *fdm = B.fdf;   // their double-float split (double-float grids)
         const TS *in = (p.in_slot == SLOT_X0 || p.in_slot == SLOT_X1)
                            ? reinterpret_cast<const TS *>(slot32(B, p.in_slot))
                            : reinterpret_cast<const TS *>(slot64(B, p.user[b], p.in_slot));
@@ -736,12 +752,11 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                 }
                 R nx = R(1), ny = R(0), nz = R(0), A = R(0);
                 if (valid) {
-                    const double *fb = fm + (long long)(fam * 4) * ml.mvolume;
-                    const long long m = fplane + (long long)fj * ml.mpitch + fi;
-                    nx = cvt<R, double>(fb[m]);
-                    ny = cvt<R, double>(fb[ml.mvolume + m]);
-                    nz = cvt<R, double>(fb[2 * ml.mvolume + m]);
-                    A = cvt<R, double>(fb[3 * ml.mvolume + m]);
+                    const long long m = (long long)(fam * 4) * ml.mvolume + fplane + (long long)fj * ml.mpitch + fi;
+                    nx = face_metric<R>(fm, fdm, m);
+                    ny = face_metric<R>(fm, fdm, ml.mvolume + m);
+                    nz = face_metric<R>(fm, fdm, 2 * ml.mvolume + m);
+                    A = face_metric<R>(fm, fdm, 3 * ml.mvolume + m);
                 }
                 face_flux(Lf, Rf, nx, ny, nz, A, gm1, kg, p.fix, cons, F);
                 if (e < NKF) {
