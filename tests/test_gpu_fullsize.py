@@ -1,0 +1,176 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+bench times (the autotuned schedule; steps as CUDA-graph replays):
+
+  periodic 3D 256^3: the whole FP64 and double-float residuals against the
+    oracle's, element by element (1e-11; double-float 32e-11); dt of the CFL
+    step against the oracle's (1e-13: the volume formula's cancellation
+    grows with n); one SSPRK3 step replayed from a graph against the
+    oracle's step on sampled sub-boxes (their cores, 6 cells inside the cut
+    faces: 1e-11);
+  64-block lattice (interfaces, inflow, wall, extrapolation, periodic): the
+    whole FP64 residual of every block against the oracle's (1e-11 of each
+    variable's scale over the lattice); one
+    FP32-flux graph step within density L2 1e-5 of the FP64 step;
+  512^3 ramp: the FP64 residual on sampled sub-boxes (corners on the inflow,
+    wall, outflow, top and periodic faces, the ramp corner, the interior)
+    against the oracle's (1e-11 of the sampled residual's scale); one
+    FP32-storage graph step within density L2 1e-5 of the FP64 step.
+The mixed forms are held to their bar against the FP64 path, which the same
+test first holds to the oracle.
+"""
+import gc
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import gpu_grid, gpu_states, oracle_grid, oracle_states, oracle_subbox, per_var_rel
+from paper_2305_18057_gb300 import sensei, workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _tuned(w, precision):
+    g = gpu_grid(w, precision=precision)
+    Us = gpu_states(g, w)
+    g.autotune(Us)
+    torch.cuda.synchronize()
+    return g, Us
+
+
+def _residual(g, w, Us):
+    Rs = [torch.empty((5, nk, nj, ni), dtype=torch.float64, device=Us[0].device) for ni, nj, nk in w.dims]
+    g.residual(Us, Rs)
+    torch.cuda.synchronize()
+    return Rs
+
+
+def _graph_step(g, Us, cfl=0.5, dt=0.0):
+    dt_used = torch.zeros(1, dtype=torch.float64, device=Us[0].device)
+    graph = g.step_graph(Us, sensei.RK3_SSP, cfl=cfl, dt=dt, dt_used=dt_used)
+    graph.launch()
+    torch.cuda.synchronize()
+    graph.close()
+    return dt_used.item()
+
+
+def _free():
+    gc.collect()
+    torch.cuda.empty_cache()
+
+
+def _core_boxes(n, margin=6, size=10):
+    """Enlarged boxes (size + 2 margin) strictly inside an n^3 periodic block
+    and their cores."""
+    e = size + 2 * margin
+    starts = [(0, 0, 0), (n - e, n - e, n - e), (n // 2 - e // 2, 3, n - e - 5), (7, n // 3, n // 2)]
+    return [((i, j, k), (i + e, j + e, k + e)) for i, j, k in starts]
+
+
+def test_periodic3d_256_full_residual_dt_and_graph_step():
+    w = wl.periodic_3d(n=256)
+    n = 256
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    Ro = og.residual(Uo)[0]
+    dt_o = 0.5 * og.dt_min(Uo, fill=False)
+    del og, Uo
+    _free()
+    # FP64: 1e-11.  Double-float carries 48 bits (unit roundoff 2^-48, 32
+    # times FP64's), and on this smooth 256^3 field the residual is ~1e-3 of
+    # the face fluxes it is the difference of, so its bar is the FP64 bar
+    # scaled by the roundoff ratio: 32e-11 (measured 3.9e-11; FP64 ~1e-12)
+    for precision, tol in ((sensei.FP64, 1e-11), (sensei.DF64, 32e-11)):
+        g, Us = _tuned(w, precision)
+        R = _residual(g, w, Us)[0].cpu().numpy()
+        assert per_var_rel(R, Ro) < tol, precision
+        del g, Us, R
+        _free()
+    # one SSPRK3 step as the bench replays it
+    g, Us = _tuned(w, sensei.FP64)
+    dt = _graph_step(g, Us)
+    # dt carries |Omega| = 1/3 sum_f xbar_f . S_f, whose terms are ~|x| h^2
+    # for a volume h^3: a cancellation of ~1/h = 256 here, so two FP64
+    # evaluations in different orders agree to ~256 x a few ulp, not to the
+    # 1e-14 of the small cases (measured 1.8e-14)
+    assert abs(dt - dt_o) <= 1e-13 * dt_o
+    U1 = g.download(Us[0], 0)
+    del g, Us
+    _free()
+    for lo, hi in _core_boxes(n):
+        sg, U = oracle_subbox(w, 0, lo, hi, w.U0[0])
+        sg.rk_step([U], oracle.RK3_SSP, dt=dt_o)
+        want = sg.interior(U, 0)[:, 6:-6, 6:-6, 6:-6]
+        got = U1[:, lo[2] + 6:hi[2] - 6, lo[1] + 6:hi[1] - 6, lo[0] + 6:hi[0] - 6]
+        assert per_var_rel(got, want) < 1e-11, (lo, hi)
+
+
+def test_lattice_full_residual_and_fp32_flux_step():
+    w = wl.lattice_3d()
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    Ro = og.residual(Uo)
+    del og, Uo
+    _free()
+    g, Us = _tuned(w, sensei.FP64)
+    Rs = _residual(g, w, Us)
+    # one residual field over the 64 blocks, each variable on its scale over
+    # all of them (the blocks in uniform inflow hold round-off only, ~1e-13
+    # on fluxes of a few hundred)
+    got = np.concatenate([R.cpu().numpy().reshape(5, -1) for R in Rs], axis=1)
+    want = np.concatenate([R.reshape(5, -1) for R in Ro], axis=1)
+    assert per_var_rel(got, want) < 1e-11
+    del Rs, got, want
+    dt = _graph_step(g, Us)
+    want = [g.download(U, b)[0] for b, U in enumerate(Us)]
+    del g, Us
+    _free()
+    g, Us = _tuned(w, sensei.FP32_FLUX)
+    _graph_step(g, Us, cfl=0.0, dt=dt)
+    got = [g.download(U, b)[0] for b, U in enumerate(Us)]
+    num = sum(float(np.sum((a - b) ** 2)) for a, b in zip(got, want))
+    den = sum(float(np.sum(b ** 2)) for b in want)
+    assert np.sqrt(num / den) <= 1e-5
+    del g, Us
+    _free()
+
+
+RAMP512_BOXES = [
+    ((0, 0, 0), (16, 16, 12)),            # inflow / wall / periodic k corner
+    ((496, 496, 500), (512, 512, 512)),   # outflow / top inflow / periodic k corner
+    ((0, 496, 200), (16, 512, 216)),      # inflow / top
+    ((496, 0, 300), (512, 16, 316)),      # outflow / wall
+    ((120, 0, 40), (140, 12, 52)),        # the wall around the ramp corner
+    ((250, 200, 250), (266, 216, 266)),   # interior
+]
+
+
+def test_ramp512_sampled_residual_and_fp32_storage_step():
+    w = wl.ramp_3d(n=512)
+    g, Us = _tuned(w, sensei.FP64)
+    R = _residual(g, w, Us)[0]
+    got, want = [], []
+    for lo, hi in RAMP512_BOXES:
+        sg, U = oracle_subbox(w, 0, lo, hi, w.U0[0])
+        want.append(sg.residual([U], fill=False)[0])
+        got.append(R[:, lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].cpu().numpy())
+    del R
+    # all sampled cells together, each variable on its own scale (floored
+    # for a variable that is zero up to round-off, as everywhere)
+    got_all = np.concatenate([a.reshape(5, -1) for a in got], axis=1)
+    want_all = np.concatenate([b.reshape(5, -1) for b in want], axis=1)
+    assert np.abs(want_all).max() > 0
+    assert per_var_rel(got_all, want_all) < 1e-11
+    # the mixed form the bench measures on this grid: FP32 stage states and
+    # flux, FP64 accumulation, one step at the FP64 step's dt
+    dt = _graph_step(g, Us)
+    rho64 = g.download(Us[0], 0)[0]
+    del g, Us
+    _free()
+    g, Us = _tuned(w, sensei.FP32_STORE)
+    _graph_step(g, Us, cfl=0.0, dt=dt)
+    rho32 = g.download(Us[0], 0)[0]
+    assert np.linalg.norm(rho32 - rho64) / np.linalg.norm(rho64) <= 1e-5
+    del g, Us
+    _free()
