@@ -147,11 +147,13 @@ static void quad_area(const double p0[3], const double p1[3], const double p2[3]
     S[2] = 0.5 * c[2];
 }
 
-static void quad_centroid(const double p0[3], const double p1[3], const double p2[3],
-                          const double p3[3], double c[3])
+/* Centroid of the four corners measured from the point o: the corners'
+ * offsets from o are formed first (exact for nearby points), then averaged. */
+static void quad_centroid_from(const double p0[3], const double p1[3], const double p2[3],
+                               const double p3[3], const double o[3], double c[3])
 {
     for (int a = 0; a < 3; ++a)
-        c[a] = 0.25 * (p0[a] + p1[a] + p2[a] + p3[a]);
+        c[a] = 0.25 * ((p0[a] - o[a]) + (p1[a] - o[a]) + (p2[a] - o[a]) + (p3[a] - o[a]));
 }
 
 /* The corner nodes of the three face families, ordered so that the area
@@ -204,24 +206,31 @@ static void compute_metrics(ora_block *b, const double *X)
                 for (int a = 0; a < 3; ++a) b->Sk[a * nfk + fk_index(b, i, j, k)] = S[a];
             }
     /* |Omega| = (1/3) * sum over the six faces of  centroid . outward area
-     * vector (divergence theorem applied to the position vector). */
+     * vector (divergence theorem applied to the position vector).  The
+     * position is measured from the cell's corner node (i, j, k): the closed
+     * surface's area vectors sum to zero, so any origin gives the same
+     * volume, and a corner of the cell keeps every term of the cell's own
+     * size (measured from the coordinate origin, terms of size |x| h^2 would
+     * cancel to a volume h^3, losing a factor |x|/h of accuracy). */
     for (int k = 0; k < b->nk; ++k)
         for (int j = 0; j < b->nj; ++j)
             for (int i = 0; i < b->ni; ++i) {
+                double o[3];
+                get_node(X, b, i, j, k, o);
                 double v = 0.0;
                 for (int side = 0; side < 2; ++side) {
                     double sgn = side ? 1.0 : -1.0;
                     iface_nodes(X, b, i + side, j, k, p);
                     quad_area(p[0], p[1], p[2], p[3], S);
-                    quad_centroid(p[0], p[1], p[2], p[3], c);
+                    quad_centroid_from(p[0], p[1], p[2], p[3], o, c);
                     v += sgn * (c[0] * S[0] + c[1] * S[1] + c[2] * S[2]);
                     jface_nodes(X, b, i, j + side, k, p);
                     quad_area(p[0], p[1], p[2], p[3], S);
-                    quad_centroid(p[0], p[1], p[2], p[3], c);
+                    quad_centroid_from(p[0], p[1], p[2], p[3], o, c);
                     v += sgn * (c[0] * S[0] + c[1] * S[1] + c[2] * S[2]);
                     kface_nodes(X, b, i, j, k + side, p);
                     quad_area(p[0], p[1], p[2], p[3], S);
-                    quad_centroid(p[0], p[1], p[2], p[3], c);
+                    quad_centroid_from(p[0], p[1], p[2], p[3], o, c);
                     v += sgn * (c[0] * S[0] + c[1] * S[1] + c[2] * S[2]);
                 }
                 b->vol[interior(b, i, j, k)] = v / 3.0;
