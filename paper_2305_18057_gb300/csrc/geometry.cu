@@ -32,9 +32,14 @@ __device__ __forceinline__ P3 quad_area(P3 a, P3 b, P3 c, P3 d)
     return P3{0.5 * (e.y * f.z - e.z * f.y), 0.5 * (e.z * f.x - e.x * f.z), 0.5 * (e.x * f.y - e.y * f.x)};
 }
 
-__device__ __forceinline__ double centroid_dot(P3 a, P3 b, P3 c, P3 d, P3 s)
+// (centroid - o) . s with the corners' offsets from o formed first (exact
+// for nearby points)
+__device__ __forceinline__ double centroid_dot(P3 a, P3 b, P3 c, P3 d, P3 o, P3 s)
 {
-    return 0.25 * ((a.x + b.x + c.x + d.x) * s.x + (a.y + b.y + c.y + d.y) * s.y + (a.z + b.z + c.z + d.z) * s.z);
+    const double cx = (a.x - o.x) + (b.x - o.x) + (c.x - o.x) + (d.x - o.x);
+    const double cy = (a.y - o.y) + (b.y - o.y) + (c.y - o.y) + (d.y - o.y);
+    const double cz = (a.z - o.z) + (b.z - o.z) + (c.z - o.z) + (d.z - o.z);
+    return 0.25 * (cx * s.x + cy * s.y + cz * s.z);
 }
 
 // Corners of the three face families at lowest node (i, j, k), ordered so
@@ -89,8 +94,13 @@ __global__ void metrics_kernel(int ni, int nj, int nk, const double *__restrict_
         }
         if (in_i && in_j && in_k) {
             // |Omega| = (1/3) sum over the six faces of centroid . outward area
-            // vector; the mean area vector of the two d-faces gives the
-            // spectral radius of the time-step bound.
+            // vector, the centroids measured from the cell's corner node (the
+            // area vectors of the closed cell sum to zero, so the origin does
+            // not change the volume, and a corner of the cell keeps every term
+            // of the cell's size instead of |x| h^2 terms cancelling to h^3);
+            // the mean area vector of the two d-faces gives the spectral
+            // radius of the time-step bound.
+            const P3 o = load_node(X, nn, ni, nj, i, j, k);
             double vol = 0.0;
             for (int fam = 0; fam < 3; ++fam) {
                 int di = fam == 0, dj = fam == 1, dk = fam == 2;
@@ -98,8 +108,8 @@ __global__ void metrics_kernel(int ni, int nj, int nk, const double *__restrict_
                 FaceCorners hi = corners(X, nn, ni, nj, fam, i + di, j + dj, k + dk);
                 P3 slo = quad_area(lo.p[0], lo.p[1], lo.p[2], lo.p[3]);
                 P3 shi = quad_area(hi.p[0], hi.p[1], hi.p[2], hi.p[3]);
-                vol += centroid_dot(hi.p[0], hi.p[1], hi.p[2], hi.p[3], shi) -
-                       centroid_dot(lo.p[0], lo.p[1], lo.p[2], lo.p[3], slo);
+                vol += centroid_dot(hi.p[0], hi.p[1], hi.p[2], hi.p[3], o, shi) -
+                       centroid_dot(lo.p[0], lo.p[1], lo.p[2], lo.p[3], o, slo);
                 P3 sb{0.5 * (slo.x + shi.x), 0.5 * (slo.y + shi.y), 0.5 * (slo.z + shi.z)};
                 mo.sbar[fam][0][m] = sb.x;
                 mo.sbar[fam][1][m] = sb.y;

@@ -3,8 +3,7 @@ bench times (the autotuned schedule; steps as CUDA-graph replays):
 
   periodic 3D 256^3: the whole FP64 and double-float residuals against the
     oracle's, element by element (1e-11; double-float 32e-11); dt of the CFL
-    step against the oracle's (1e-13: the volume formula's cancellation
-    grows with n); one SSPRK3 step replayed from a graph against the
+    step against the oracle's (1e-14); one SSPRK3 step replayed from a graph against the
     oracle's step on sampled sub-boxes (their cores, 6 cells inside the cut
     faces: 1e-11);
   64-block lattice (interfaces, inflow, wall, extrapolation, periodic): the
@@ -90,11 +89,7 @@ def test_periodic3d_256_full_residual_dt_and_graph_step():
     # one SSPRK3 step as the bench replays it
     g, Us = _tuned(w, sensei.FP64)
     dt = _graph_step(g, Us)
-    # dt carries |Omega| = 1/3 sum_f xbar_f . S_f, whose terms are ~|x| h^2
-    # for a volume h^3: a cancellation of ~1/h = 256 here, so two FP64
-    # evaluations in different orders agree to ~256 x a few ulp, not to the
-    # 1e-14 of the small cases (measured 1.8e-14)
-    assert abs(dt - dt_o) <= 1e-13 * dt_o
+    assert abs(dt - dt_o) <= 1e-14 * dt_o
     U1 = g.download(Us[0], 0)
     del g, Us
     _free()
@@ -172,5 +167,35 @@ def test_ramp512_sampled_residual_and_fp32_storage_step():
     _graph_step(g, Us, cfl=0.0, dt=dt)
     rho32 = g.download(Us[0], 0)[0]
     assert np.linalg.norm(rho32 - rho64) / np.linalg.norm(rho64) <= 1e-5
+    del g, Us
+    _free()
+
+
+@pytest.mark.parametrize("name,make,steps", [
+    ("advection2d 128^2", lambda: wl.advection_2d(n=128), 200),
+    ("ramp2d 1024x512", lambda: wl.ramp_2d(ni=1024, nj=512), 10),
+])
+def test_2d_full_size_residual_and_graph_steps(name, make, steps):
+    """The 2D workloads whole: the residual (1e-11) and the state after
+    their steps replayed from a graph, CFL mode, the oracle stepping with
+    its own dt (1e-9)."""
+    w = make()
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    Ro = og.residual(Uo)[0]
+    g, Us = _tuned(w, sensei.FP64)
+    R = _residual(g, w, Us)[0].cpu().numpy()
+    assert per_var_rel(R, Ro) < 1e-11, name
+    dt_used = torch.zeros(1, dtype=torch.float64, device=Us[0].device)
+    graph = g.step_graph(Us, sensei.RK3_SSP, cfl=0.5, dt_used=dt_used)
+    for n in range(steps):
+        graph.launch()
+        dt_o, _ = og.rk_step(Uo, oracle.RK3_SSP, cfl=0.5)
+        if n == 0:
+            torch.cuda.synchronize()
+            assert abs(dt_used.item() - dt_o) <= 1e-14 * dt_o, name
+    torch.cuda.synchronize()
+    graph.close()
+    assert per_var_rel(g.download(Us[0], 0), og.interior(Uo[0], 0)) < 1e-9, name
     del g, Us
     _free()
