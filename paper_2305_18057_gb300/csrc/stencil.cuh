@@ -76,6 +76,16 @@ __device__ __forceinline__ double rcp_nr(double d)
     return r;
 }
 
+// x / 2 for a positive normal x (x >= 2^-1021): FP64 lowers the exponent
+// by one on the integer pipe, off the narrow FP64 pipe (exact); FP32 and
+// double-float multiply by 0.5 on the FP32 pipe (exact)
+__device__ __forceinline__ double half_pos(double x)
+{
+    return __hiloint2double(__double2hiint(x) - 0x00100000, __double2loint(x));
+}
+__device__ __forceinline__ float half_pos(float x) { return 0.5f * x; }
+__device__ __forceinline__ df64 half_pos(df64 x) { return df64(0.5f * x.hi, 0.5f * x.lo); }
+
 template <int STEPS>
 __device__ __forceinline__ double rsqrt_nr(double x)
 {
@@ -84,7 +94,7 @@ __device__ __forceinline__ double rsqrt_nr(double x)
 #pragma unroll
     for (int n = 0; n < STEPS; ++n) {
         double e = fma(-(x * y), y, 1.0);
-        y = fma(0.5 * y, e, y);
+        y = fma(half_pos(y), e, y);
     }
     return y;
 }
@@ -286,6 +296,10 @@ __device__ __forceinline__ void face_states(R wm, R w0, R wp, R c1, R c2, R half
 // Roe flux through a face of unit normal n and area A between primitive
 // states wl, wr: A/2 [F(wl) + F(wr) - sum_k |lam_k| alpha_k r_k], three-wave
 // form, Harten's entropy fix on the acoustic waves (delta = fix * a).
+// Arranged for few operations: A/2 joins the wave speeds, so the flux is
+// one fused multiply-add per component; the energy row of the dissipation
+// uses D_4 = u . (D_1, D_2, D_3) + (H - q^2) s13 - q^2/2 c2 (exact algebra
+// on the three-wave sum); halvings of positive values on the integer pipe.
 template <typename R>
 __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R ny, R nz, R A, R gm1, R kg,
                                          R fix, R F[NV])
@@ -294,8 +308,8 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     const R rr = wr[0], ur = wr[1], vr = wr[2], zr = wr[3], pr = wr[4];
     const R vnl = nx * ul + ny * vl + nz * zl;
     const R vnr = nx * ur + ny * vr + nz * zr;
-    const R rhl = kg * pl + R(0.5) * rl * (ul * ul + vl * vl + zl * zl);   // rho h_t
-    const R rhr = kg * pr + R(0.5) * rr * (ur * ur + vr * vr + zr * zr);
+    const R rhl = kg * pl + half_pos(rl) * (ul * ul + vl * vl + zl * zl);   // rho h_t
+    const R rhr = kg * pr + half_pos(rr) * (ur * ur + vr * vr + zr * zr);
     const R ml = rl * vnl, mr = rr * vnr;
     const R psum = pl + pr;
     R c[NV];
@@ -305,48 +319,54 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     c[3] = ml * zl + mr * zr + nz * psum;
     c[4] = rhl * vnl + rhr * vnr;
     // Roe average with weights sqrt(rho): with q = 1/sqrt(rl rr) and
-    // t = sqrt(rr/rl) = rr q, the weights are 1/(1+t) and t/(1+t), the
-    // averaged density sqrt(rl rr) = rl rr q and the averaged enthalpy
+    // t = sqrt(rr/rl) = rr q, phi = (phi_l + t phi_r)/(1+t), the averaged
+    // density sqrt(rl rr) = rl rr q and the averaged enthalpy
     // (H_l + t H_r)/(1+t) with H_l + t H_r = (rhl rr + t rhr rl) q^2.
     // These only enter the dissipation term: one Newton step suffices.
     const R rlr = rl * rr;
     const R qq = rsqrt1_t(rlr);
     const R t = rr * qq;
     const R wL = rcp_t<R, 1>(R(1) + t);
-    const R wR = t * wL;
-    const R u = wL * ul + wR * ur, v = wL * vl + wR * vr, w = wL * zl + wR * zr;
+    const R u = wL * (ul + t * ur), v = wL * (vl + t * vr), w = wL * (zl + t * zr);
     const R H = wL * ((rhl * rr + (t * rhr) * rl) * (qq * qq));
     const R rho = rlr * qq;
     const R q2 = u * u + v * v + w * w;
-    const R a2 = gm1 * (H - R(0.5) * q2);
+    const R hq2 = R(0.5) * q2;
+    const R a2 = gm1 * (H - hq2);
     const R ia = rsqrt1_t(a2);
     const R a = a2 * ia;
     const R ia2 = ia * ia;
     const R vn = nx * u + ny * v + nz * w;
     const R dr = rr - rl, dp = pr - pl, du = ur - ul, dv = vr - vl, dw = zr - zl, dvn = vnr - vnl;
     R l1 = fabs(vn - a), l3 = fabs(vn + a);
-    const R l2 = fabs(vn);
+    R l2 = fabs(vn);
     const R delta = fix * a;
     // |lambda| < delta on the integer pipe (both are >= 0)
     if (lt_nonneg(l1, delta)) l1 = R(0.5) * (l1 * l1 * (ia / fix) + delta);
     if (lt_nonneg(l3, delta)) l3 = R(0.5) * (l3 * l3 * (ia / fix) + delta);
+    // the wave speeds times A/2
+    const R h = R(0.5) * A;
+    l1 = h * l1;
+    l2 = h * l2;
+    l3 = h * l3;
     const R rad = rho * a * dvn;
-    const R c1w = l1 * (R(0.5) * (dp - rad) * ia2);
-    const R c3w = l3 * (R(0.5) * (dp + rad) * ia2);
+    const R hia2 = half_pos(ia2);
+    const R c1w = l1 * ((dp - rad) * hia2);
+    const R c3w = l3 * ((dp + rad) * hia2);
     const R c2w = l2 * (dr - dp * ia2);
     const R cs = l2 * rho;
     const R s13 = c1w + c3w, d13 = c3w - c1w;
     const R D0 = s13 + c2w;
     const R g = a * d13 - cs * dvn;
-    R D[NV];
-    D[0] = D0;
-    D[1] = u * D0 + nx * g + cs * du;
-    D[2] = v * D0 + ny * g + cs * dv;
-    D[3] = w * D0 + nz * g + cs * dw;
-    D[4] = H * s13 + a * vn * d13 + R(0.5) * q2 * c2w + cs * (u * du + v * dv + w * dw - vn * dvn);
-    const R h = R(0.5) * A;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) F[q] = h * (c[q] - D[q]);
+    const R D1 = u * D0 + nx * g + cs * du;
+    const R D2 = v * D0 + ny * g + cs * dv;
+    const R D3 = w * D0 + nz * g + cs * dw;
+    const R D4 = u * D1 + v * D2 + w * D3 + (H - q2) * s13 - hq2 * c2w;
+    F[0] = fma(h, c[0], -D0);
+    F[1] = fma(h, c[1], -D1);
+    F[2] = fma(h, c[2], -D2);
+    F[3] = fma(h, c[3], -D3);
+    F[4] = fma(h, c[4], -D4);
 }
 
 // The face flux from the two reconstructed states (primitive, or conserved
