@@ -463,6 +463,7 @@ void fill_params(BatchParams<R> &p, const sensei_grid *g, const StencilCall &c)
     p.kappa = (R)g->scheme.kappa;
     p.eps = (R)g->scheme.eps;
     p.fix = (R)g->scheme.entropy_fix;
+    p.ifix = (R)(g->scheme.entropy_fix > 0.0 ? 1.0 / g->scheme.entropy_fix : 0.0);
     // the derived constants, in R arithmetic as the kernels would form them
     p.gm1 = p.gamma - (R)1;
     p.kg = p.gamma / p.gm1;

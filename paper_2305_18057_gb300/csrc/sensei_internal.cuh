@@ -128,6 +128,7 @@ struct BatchParams {
     int push;
     int local;              // local time stepping: the stage step is dtv[cell], not dt / |Omega|
     R gamma, kappa, eps, fix;
+    R ifix;                 // 1 / fix (0 when fix is 0: the entropy fix never applies)
     R gm1, kg, c1, c2, half_eps;   // gamma - 1, gamma / (gamma - 1), eps (1 -+ kappa) / 4, eps / 2 in R
     int cons;
     int vis;                // subtract the viscous residual B.rvis

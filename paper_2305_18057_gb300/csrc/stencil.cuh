@@ -86,6 +86,15 @@ __device__ __forceinline__ double half_pos(double x)
 __device__ __forceinline__ float half_pos(float x) { return 0.5f * x; }
 __device__ __forceinline__ df64 half_pos(df64 x) { return df64(0.5f * x.hi, 0.5f * x.lo); }
 
+// |x| with the sign bit cleared on the integer pipe (FP64); FP32 and
+// double-float as usual
+__device__ __forceinline__ double abs_bits(double x)
+{
+    return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
+}
+__device__ __forceinline__ float abs_bits(float x) { return fabsf(x); }
+__device__ __forceinline__ df64 abs_bits(df64 x) { return fabs(x); }
+
 template <int STEPS>
 __device__ __forceinline__ double rsqrt_nr(double x)
 {
@@ -302,7 +311,7 @@ __device__ __forceinline__ void face_states(R wm, R w0, R wp, R c1, R c2, R half
 // on the three-wave sum); halvings of positive values on the integer pipe.
 template <typename R>
 __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R ny, R nz, R A, R gm1, R kg,
-                                         R fix, R F[NV])
+                                         R fix, R ifix, R F[NV])
 {
     const R rl = wl[0], ul = wl[1], vl = wl[2], zl = wl[3], pl = wl[4];
     const R rr = wr[0], ur = wr[1], vr = wr[2], zr = wr[3], pr = wr[4];
@@ -338,12 +347,13 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     const R ia2 = ia * ia;
     const R vn = nx * u + ny * v + nz * w;
     const R dr = rr - rl, dp = pr - pl, du = ur - ul, dv = vr - vl, dw = zr - zl, dvn = vnr - vnl;
-    R l1 = fabs(vn - a), l3 = fabs(vn + a);
-    R l2 = fabs(vn);
+    R l1 = abs_bits(vn - a), l3 = abs_bits(vn + a);
+    R l2 = abs_bits(vn);
     const R delta = fix * a;
     // |lambda| < delta on the integer pipe (both are >= 0)
-    if (lt_nonneg(l1, delta)) l1 = R(0.5) * (l1 * l1 * (ia / fix) + delta);
-    if (lt_nonneg(l3, delta)) l3 = R(0.5) * (l3 * l3 * (ia / fix) + delta);
+    // (lambda^2 / delta + delta) / 2 with 1/delta = ia / fix
+    if (lt_nonneg(l1, delta)) l1 = R(0.5) * (l1 * l1 * (ia * ifix) + delta);
+    if (lt_nonneg(l3, delta)) l3 = R(0.5) * (l3 * l3 * (ia * ifix) + delta);
     // the wave speeds times A/2
     const R h = R(0.5) * A;
     l1 = h * l1;
@@ -374,7 +384,7 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
 // One inlined copy of the Roe flux per call site (the branch only converts
 // the states).
 template <typename R>
-__device__ __forceinline__ void face_flux(R L[NV], R Rt[NV], R nx, R ny, R nz, R A, R gm1, R kg, R fix, int cons,
+__device__ __forceinline__ void face_flux(R L[NV], R Rt[NV], R nx, R ny, R nz, R A, R gm1, R kg, R fix, R ifix, int cons,
                                           R F[NV])
 {
     R wl[NV], wr[NV];
@@ -388,7 +398,7 @@ __device__ __forceinline__ void face_flux(R L[NV], R Rt[NV], R nx, R ny, R nz, R
             wr[v] = Rt[v];
         }
     }
-    roe_flux(wl, wr, nx, ny, nz, A, gm1, kg, fix, F);
+    roe_flux(wl, wr, nx, ny, nz, A, gm1, kg, fix, ifix, F);
 }
 
 // Loads a cell of the stage input (storage type TS) as the arithmetic type R.
@@ -778,7 +788,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                     nz = face_metric<R>(fm, fdm, 2 * ml.mvolume + m);
                     A = face_metric<R>(fm, fdm, 3 * ml.mvolume + m);
                 }
-                face_flux(Lf, Rf, nx, ny, nz, A, gm1, kg, p.fix, cons, F);
+                face_flux(Lf, Rf, nx, ny, nz, A, gm1, kg, p.fix, p.ifix, cons, F);
                 if (e < NKF) {
 #pragma unroll
                     for (int v = 0; v < NV; ++v) Fkp[v] = F[v];

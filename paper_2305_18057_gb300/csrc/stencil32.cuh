@@ -164,7 +164,8 @@ __device__ __forceinline__ void load_cell(const TS *in, const StateLayout &L, in
 // right state the minus state of a+1 (Eq. flux), metrics at met[q * mst].
 template <int LIM>
 __device__ __forceinline__ void line_flux(const float *w, int st, const float *met, int mst, float gm1, float kg,
-                                          float fix, float c1, float c2, float half_eps, int cons, float F[NV])
+                                          float fix, float ifix, float c1, float c2, float half_eps, int cons,
+                                          float F[NV])
 {
     float Lf[NV], Rf[NV];
 #pragma unroll
@@ -175,7 +176,7 @@ __device__ __forceinline__ void line_flux(const float *w, int st, const float *m
         face_states<float, LIM>(w0, w1, w2, c1, c2, half_eps, Lf[v], unused);
         face_states<float, LIM>(w1, w2, w3, c1, c2, half_eps, unused, Rf[v]);
     }
-    face_flux(Lf, Rf, met[0], met[mst], met[2 * mst], met[3 * mst], gm1, kg, fix, cons, F);
+    face_flux(Lf, Rf, met[0], met[mst], met[2 * mst], met[3 * mst], gm1, kg, fix, ifix, cons, F);
 }
 
 // s + (hi, lo) in double-single arithmetic (Knuth's two-sum, then a
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
 #define c2 p.c2
 #define half_eps p.half_eps
 #define fix p.fix
+#define ifix p.ifix
 #define cons p.cons
     const bool update = p.mode != MODE_RESIDUAL;
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
             const double *f2 = B.fn + 8 * ml.mvolume;
             float Fkm[NV];
             face_flux(Lk, Rk, to_f32(f2[fk]), to_f32(f2[ml.mvolume + fk]), to_f32(f2[2 * ml.mvolume + fk]),
-                      to_f32(f2[3 * ml.mvolume + fk]), gm1, kg, fix, cons, Fkm);
+                      to_f32(f2[3 * ml.mvolume + fk]), gm1, kg, fix, ifix, cons, Fkm);
 #pragma unroll
             for (int v = 0; v < NV; ++v) sFkm[v * NTHREADS + t] = Fkm[v];
         }
@@ -427,7 +429,8 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
                     face_states<float, LIM>(sW[v * TPLANE + (tj + 2) * TW + ti + 2], sK[(kb * NV + v) * NTHREADS + t],
                                             sK[((kb ^ 1) * NV + v) * NTHREADS + t], c1, c2, half_eps, Ppn[v], Rk[v]);
                 const float *mk = met + REC_I + REC_J + tj * TI + ti;
-                face_flux(Pp, Rk, mk[0], mk[TJ * TI], mk[2 * TJ * TI], mk[3 * TJ * TI], gm1, kg, fix, cons, Fkp);
+                face_flux(Pp, Rk, mk[0], mk[TJ * TI], mk[2 * TJ * TI], mk[3 * TJ * TI], gm1, kg, fix, ifix, cons,
+                          Fkp);
             }
             float Fi[NV];
 #pragma unroll 1
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
                     mst = TJ * (TI + 1);
                 }
                 float F[NV];
-                line_flux<LIM>(w, st, mt, mst, gm1, kg, fix, c1, c2, half_eps, cons, F);
+                line_flux<LIM>(w, st, mt, mst, gm1, kg, fix, ifix, c1, c2, half_eps, cons, F);
                 if (dst) {
 #pragma unroll
                     for (int v = 0; v < NV; ++v) dst[v * dstv] = F[v];
@@ -638,6 +641,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
 #undef c2
 #undef half_eps
 #undef fix
+#undef ifix
 #undef cons
 }
 
