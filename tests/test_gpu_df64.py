@@ -70,3 +70,39 @@ def test_df64_with_viscosity():
     g.residual(Us, Rs)
     torch.cuda.synchronize()
     assert per_var_rel(Rs[0].cpu().numpy(), Ro[0]) < 1e-11
+
+
+def test_df64_step_graph_replays_eager_steps_bitwise():
+    w = CASES["lattice"]()
+    ga = gpu_grid(w, precision=sensei.DF64)
+    Ua = gpu_states(ga, w)
+    gb = gpu_grid(w, precision=sensei.DF64)
+    Ub = gpu_states(gb, w)
+    graph = gb.step_graph(Ub, oracle.RK3_SSP, cfl=0.5)
+    for _ in range(5):
+        ga.rk_step(Ua, oracle.RK3_SSP, cfl=0.5)
+        graph.launch()
+    torch.cuda.synchronize()
+    graph.close()
+    for b in range(len(w.dims)):
+        assert torch.equal(ga.interior_view(Ua[b], b), gb.interior_view(Ub[b], b)), b
+
+
+@pytest.mark.parametrize("case", ["periodic3d_odd", "ramp2d", "lattice"])
+def test_df64_local_time_stepping_and_autotune(case):
+    """Local time stepping and the autotuned schedule in the double-float
+    form, 20 steps against the oracle at the FP64 path's 1e-9."""
+    w = CASES[case]()
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    g = gpu_grid(w, precision=sensei.DF64)
+    Us = gpu_states(g, w)
+    g.autotune(Us)
+    dt_min = torch.zeros(1, dtype=torch.float64, device=Us[0].device)
+    for _ in range(20):
+        g.rk_step_local(Us, oracle.RK3_SSP, cfl=0.6, dt_min=dt_min)
+        dto, _ = og.rk_step_local(Uo, oracle.RK3_SSP, cfl=0.6)
+        assert abs(dt_min.item() - dto) <= 1e-11 * dto
+    torch.cuda.synchronize()
+    for b in range(len(w.dims)):
+        assert per_var_rel(g.download(Us[b], b), og.interior(Uo[b], b)) < 1e-9, (case, b)

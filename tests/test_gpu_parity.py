@@ -203,7 +203,7 @@ def test_local_time_stepping_converges_on_gpu():
     # the stretched Mach-4 ramp of the oracle's pin, marched to round-off
     from test_oracle_lts import _ramp
     w = _ramp()
-    for prec in (0, 2):
+    for prec in (0, 1, 2, 3):
         g = gpu_grid(w, precision=prec)
         Us = gpu_states(g, w)
         g.rk_step_local(Us, RK["rk3"], cfl=0.8)
@@ -211,5 +211,6 @@ def test_local_time_stepping_converges_on_gpu():
         for _ in range(1500):
             g.rk_step_local(Us, RK["rk3"], cfl=0.8)
         l2 = g.norms()[1][0]
-        # FP64 reaches round-off; FP32 storage stalls at its own rounding level
-        assert l2 < (1e-9 if prec == 0 else 1e-4) * l2_0, (prec, l2 / l2_0)
+        # FP64 reaches round-off, the double-float form nearly (48 bits); the
+        # FP32-flux forms stall at their own rounding level
+        assert l2 < {0: 1e-9, 3: 1e-8}.get(prec, 1e-4) * l2_0, (prec, l2 / l2_0)
