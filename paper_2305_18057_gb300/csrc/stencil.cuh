@@ -9,14 +9,17 @@
 //       limited slope computed once per cell and direction (Eq. flux; the
 //       limiter-reuse idea of Sec. 5 kept on chip instead of in a global
 //       array);
-//   P2  the Roe flux of every i- and j-face of the tile, once per face, into
-//       shared memory; the k-face above each column in registers;
+//   P2  the Roe flux of every face of the tile, once per face, through one
+//       loop and one copy of the flux code: each column's k-face above the
+//       plane (kept in registers), then the i- and j-faces (into shared
+//       memory);
 //   P3  R = sum over the faces of F.S_out - |Omega| S_h (Eq. residual), then
 //       either R is written out (residual mode) or the Runge-Kutta stage
 //       update out = alpha U^n + beta U^(s-1) - gdt dt R / |Omega| is applied
 //       (Eq. runge_kutta, Shu-Osher form), with FP64 norm partials.
-// The reconstruction/flux arithmetic type is R (double or float); the state,
-// the update and every reduction are FP64.
+// The reconstruction/flux arithmetic type is R (double, float, or the
+// double-float pair df64); the state, the update and every reduction are
+// FP64.
 #pragma once
 
 #include <math.h>
