@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from helpers import gpu_grid, gpu_states, oracle_grid, oracle_states, per_var_rel
-from paper_2305_18057_gb300 import workloads as wl
+from paper_2305_18057_gb300 import sensei, workloads as wl
 
 pytestmark = pytest.mark.gpu
 
@@ -29,10 +29,10 @@ CASES = {
 }
 
 
-def _residuals(w, limiter=None, kappa=None, recon=False, fix=None):
+def _residuals(w, limiter=None, kappa=None, recon=False, fix=None, precision=0):
     og = oracle_grid(w, limiter=limiter, kappa=kappa, recon_conserved=recon, fix=fix)
     Ro = og.residual(oracle_states(og, w))
-    g = gpu_grid(w, limiter=limiter, kappa=kappa, recon_conserved=recon, fix=fix)
+    g = gpu_grid(w, limiter=limiter, kappa=kappa, recon_conserved=recon, fix=fix, precision=precision)
     Us = gpu_states(g, w)
     Rs = [torch.empty((5, nk, nj, ni), dtype=torch.float64, device=Us[0].device) for ni, nj, nk in w.dims]
     g.residual(Us, Rs)
@@ -56,6 +56,19 @@ def test_residual_parity_options(case):
                dict(limiter="vanleer", fix=0.3, recon=True)):
         Rg, Ro, *_ = _residuals(w, **kw)
         assert per_var_rel(Rg[0], Ro[0]) < 1e-11, kw
+
+
+@pytest.mark.parametrize("precision,tol", [(sensei.DF64, 1e-11), (sensei.FP32_FLUX, 2e-4), (sensei.FP32_STORE, 2e-4)])
+def test_residual_options_in_every_precision_form(precision, tol):
+    """The unlimited kappa form, conserved reconstruction and the entropy fix
+    off or wider, in the double-float form (at the FP64 bar) and the FP32
+    forms (at their residual bar, FP32 rounding of the fluxes)."""
+    for case in ("periodic3d_odd", "ramp2d"):
+        w = CASES[case]()
+        for kw in (dict(limiter="none", kappa=-1.0), dict(limiter="minmod", recon=True),
+                   dict(limiter="vanleer", fix=0.0), dict(limiter="vanleer", fix=0.3, recon=True)):
+            Rg, Ro, *_ = _residuals(w, precision=precision, **kw)
+            assert per_var_rel(Rg[0], Ro[0]) < tol, (case, kw)
 
 
 def test_residual_with_source_and_norms():
