@@ -86,8 +86,20 @@ __host__ __device__ __forceinline__ df64 &operator+=(df64 &a, df64 b) { return a
 __host__ __device__ __forceinline__ df64 &operator-=(df64 &a, df64 b) { return a = a - b; }
 __host__ __device__ __forceinline__ df64 &operator*=(df64 &a, df64 b) { return a = a * b; }
 
-// a * b + c
-__host__ __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) { return a * b + c; }
+// a * b + c as one operation: the exact error of the high parts' product,
+// the cross terms and the sum's rounding error gathered in one correction
+// term, renormalised once (a product then a sum would renormalise twice)
+__host__ __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c)
+{
+    const float p = a.hi * b.hi;
+    float pe = df_fma(a.hi, b.hi, -p);
+    pe = df_fma(a.hi, b.lo, df_fma(a.lo, b.hi, pe));
+    float s, e;
+    two_sum(p, c.hi, s, e);
+    e += pe + c.lo;
+    fast_two_sum(s, e, s, e);
+    return df64(s, e);
+}
 
 // Newton refinement of the single-precision reciprocal: r' = r + r (1 - a r)
 __host__ __device__ __forceinline__ df64 rcp_df(df64 a)

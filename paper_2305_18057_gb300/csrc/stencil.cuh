@@ -318,18 +318,20 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
 {
     const R rl = wl[0], ul = wl[1], vl = wl[2], zl = wl[3], pl = wl[4];
     const R rr = wr[0], ur = wr[1], vr = wr[2], zr = wr[3], pr = wr[4];
-    const R vnl = nx * ul + ny * vl + nz * zl;
-    const R vnr = nx * ur + ny * vr + nz * zr;
-    const R rhl = kg * pl + half_pos(rl) * (ul * ul + vl * vl + zl * zl);   // rho h_t
-    const R rhr = kg * pr + half_pos(rr) * (ur * ur + vr * vr + zr * zr);
+    // products and sums as explicit fused multiply-adds (FP64 contracts them
+    // anyway; double-float forms each in one operation)
+    const R vnl = fma(nz, zl, fma(ny, vl, nx * ul));
+    const R vnr = fma(nz, zr, fma(ny, vr, nx * ur));
+    const R rhl = fma(half_pos(rl), fma(zl, zl, fma(vl, vl, ul * ul)), kg * pl);   // rho h_t
+    const R rhr = fma(half_pos(rr), fma(zr, zr, fma(vr, vr, ur * ur)), kg * pr);
     const R ml = rl * vnl, mr = rr * vnr;
     const R psum = pl + pr;
     R c[NV];
     c[0] = ml + mr;
-    c[1] = ml * ul + mr * ur + nx * psum;
-    c[2] = ml * vl + mr * vr + ny * psum;
-    c[3] = ml * zl + mr * zr + nz * psum;
-    c[4] = rhl * vnl + rhr * vnr;
+    c[1] = fma(nx, psum, fma(mr, ur, ml * ul));
+    c[2] = fma(ny, psum, fma(mr, vr, ml * vl));
+    c[3] = fma(nz, psum, fma(mr, zr, ml * zl));
+    c[4] = fma(rhr, vnr, rhl * vnl);
     // Roe average with weights sqrt(rho): with q = 1/sqrt(rl rr) and
     // t = sqrt(rr/rl) = rr q, phi = (phi_l + t phi_r)/(1+t), the averaged
     // density sqrt(rl rr) = rl rr q and the averaged enthalpy
@@ -339,24 +341,24 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     const R qq = rsqrt1_t(rlr);
     const R t = rr * qq;
     const R wL = rcp_t<R, 1>(R(1) + t);
-    const R u = wL * (ul + t * ur), v = wL * (vl + t * vr), w = wL * (zl + t * zr);
-    const R H = wL * ((rhl * rr + (t * rhr) * rl) * (qq * qq));
+    const R u = wL * fma(t, ur, ul), v = wL * fma(t, vr, vl), w = wL * fma(t, zr, zl);
+    const R H = wL * (fma(t * rhr, rl, rhl * rr) * (qq * qq));
     const R rho = rlr * qq;
-    const R q2 = u * u + v * v + w * w;
+    const R q2 = fma(w, w, fma(v, v, u * u));
     const R hq2 = R(0.5) * q2;
     const R a2 = gm1 * (H - hq2);
     const R ia = rsqrt1_t(a2);
     const R a = a2 * ia;
     const R ia2 = ia * ia;
-    const R vn = nx * u + ny * v + nz * w;
+    const R vn = fma(nz, w, fma(ny, v, nx * u));
     const R dr = rr - rl, dp = pr - pl, du = ur - ul, dv = vr - vl, dw = zr - zl, dvn = vnr - vnl;
     R l1 = abs_bits(vn - a), l3 = abs_bits(vn + a);
     R l2 = abs_bits(vn);
     const R delta = fix * a;
     // |lambda| < delta on the integer pipe (both are >= 0)
     // (lambda^2 / delta + delta) / 2 with 1/delta = ia / fix
-    if (lt_nonneg(l1, delta)) l1 = R(0.5) * (l1 * l1 * (ia * ifix) + delta);
-    if (lt_nonneg(l3, delta)) l3 = R(0.5) * (l3 * l3 * (ia * ifix) + delta);
+    if (lt_nonneg(l1, delta)) l1 = R(0.5) * fma(l1 * l1, ia * ifix, delta);
+    if (lt_nonneg(l3, delta)) l3 = R(0.5) * fma(l3 * l3, ia * ifix, delta);
     // the wave speeds times A/2
     const R h = R(0.5) * A;
     l1 = h * l1;
@@ -366,15 +368,15 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     const R hia2 = half_pos(ia2);
     const R c1w = l1 * ((dp - rad) * hia2);
     const R c3w = l3 * ((dp + rad) * hia2);
-    const R c2w = l2 * (dr - dp * ia2);
+    const R c2w = l2 * fma(-dp, ia2, dr);
     const R cs = l2 * rho;
     const R s13 = c1w + c3w, d13 = c3w - c1w;
     const R D0 = s13 + c2w;
-    const R g = a * d13 - cs * dvn;
-    const R D1 = u * D0 + nx * g + cs * du;
-    const R D2 = v * D0 + ny * g + cs * dv;
-    const R D3 = w * D0 + nz * g + cs * dw;
-    const R D4 = u * D1 + v * D2 + w * D3 + (H - q2) * s13 - hq2 * c2w;
+    const R g = fma(a, d13, -(cs * dvn));
+    const R D1 = fma(cs, du, fma(nx, g, u * D0));
+    const R D2 = fma(cs, dv, fma(ny, g, v * D0));
+    const R D3 = fma(cs, dw, fma(nz, g, w * D0));
+    const R D4 = fma(-hq2, c2w, fma(H - q2, s13, fma(w, D3, fma(v, D2, u * D1))));
     F[0] = fma(h, c[0], -D0);
     F[1] = fma(h, c[1], -D1);
     F[2] = fma(h, c[2], -D2);
