@@ -111,8 +111,8 @@ __host__ __device__ __forceinline__ df64 rcp_df(df64 a)
     const float r0 = 1.0f / a.hi;
 #endif
     const df64 r(r0);
-    const df64 e = df64(1.0f) - a * r;
-    return r + r * e;
+    const df64 e = fma(-a, r, df64(1.0f));
+    return fma(r, e, r);
 }
 
 // Newton refinement of the single-precision reciprocal square root:
@@ -126,8 +126,8 @@ __host__ __device__ __forceinline__ df64 rsqrt_df(df64 a)
     const float y0 = 1.0f / sqrtf(a.hi);
 #endif
     const df64 y(y0);
-    const df64 e = df64(1.0f) - a * (y * y);
-    return y + df64(0.5f * y0) * e;
+    const df64 e = fma(-a, y * y, df64(1.0f));
+    return fma(df64(0.5f * y0), e, y);
 }
 
 __host__ __device__ __forceinline__ df64 operator/(df64 a, df64 b) { return a * rcp_df(b); }

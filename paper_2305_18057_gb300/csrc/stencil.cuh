@@ -256,7 +256,7 @@ __device__ __forceinline__ bool to_prim(const R q[NV], R gm1, R w[NV])
 {
     R ir = rcp_t<R, 2>(q[0]);
     R u = q[1] * ir, v = q[2] * ir, ww = q[3] * ir;
-    R p = gm1 * (q[4] - R(0.5) * (q[1] * u + q[2] * v + q[3] * ww));
+    R p = gm1 * fma(R(-0.5), fma(q[3], ww, fma(q[2], v, q[1] * u)), q[4]);
     w[0] = q[0];
     w[1] = u;
     w[2] = v;
