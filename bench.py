@@ -108,7 +108,7 @@ def alg_bytes_per_cell(form, stage, two_d, stages=3):
 # of the 192^3 case of the periodic 3D workload (profiles/
 # stencil_traffic_periodic3d_192.md); the same tile schedule at 256^3, so the
 # traffic scales with the cells.  Re-measure when the kernel changes.
-MEASURED_TRAFFIC_B_PER_CELL = {"fp64": 229.3, "fp32_flux": 180.6}
+MEASURED_TRAFFIC_B_PER_CELL = {"fp64": 226.6, "fp32_flux": 180.8}
 
 
 def measured_peaks():

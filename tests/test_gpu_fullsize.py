@@ -83,7 +83,9 @@ def test_periodic3d_256_full_residual_dt_and_graph_step():
     for precision, tol in ((sensei.FP64, 1e-11), (sensei.DF64, 32e-11)):
         g, Us = _tuned(w, precision)
         R = _residual(g, w, Us)[0].cpu().numpy()
-        assert per_var_rel(R, Ro) < tol, precision
+        err = per_var_rel(R, Ro)
+        print(f"periodic3d 256^3 residual, precision {precision}: {err:.3g} of the oracle's")
+        assert err < tol, precision
         del g, Us, R
         _free()
     # one SSPRK3 step as the bench replays it
