@@ -27,16 +27,11 @@
 #include "blocks.cuh"
 #include "df64.cuh"
 
-// CTAs per SM the register allocation must allow: 2 for FP64 arithmetic
-// (the FP64 pipe is the bound; more warps cover its dependent latency), 3
-// for FP32 arithmetic (latency bound: more resident warps hide the loads).
+// CTAs per SM the register allocation must allow: 2 (FP64 and double-float
+// arithmetic; shared memory, 107 KB per CTA, allows no more).
 template <typename R>
 struct MinCtas {
     static constexpr int value = 2;
-};
-template <>
-struct MinCtas<float> {
-    static constexpr int value = 3;
 };
 
 namespace sensei {
