@@ -100,8 +100,10 @@ __device__ __forceinline__ bool face_of(const BlockDev &B, int d, long long m, i
 
 // grad xi_a at every d-face, a = d, e, f (the face's normal, then its two
 // tangential index directions): (Sbar_a(L) + Sbar_a(R)) / (|Omega_L| +
-// |Omega_R|), into gvis[(d * 9 + a * 3 + c) * mvolume + m].  Depends on the
-// boundary rules (the geometry a ghost cell carries): rerun when they change.
+// |Omega_R|), into gvis[(d * 9 + a * 3 + c) * mvolume + m]; the tangential
+// two already times the 1/4 of their central differences (exact).  Depends
+// on the boundary rules (the geometry a ghost cell carries): rerun when they
+// change.
 __global__ void vis_metrics_kernel(const BlockDev *blocks)
 {
     const int b = blockIdx.y, d = blockIdx.z;
@@ -122,9 +124,10 @@ __global__ void vis_metrics_kernel(const BlockDev *blocks)
             const bool on = dirs[a] < ndir;
             const double *sa = bL->sbar + (long long)(dirs[a] * 4) * bL->ml.mvolume + mL;
             const double *sb = bR->sbar + (long long)(dirs[a] * 4) * bR->ml.mvolume + mR;
+            const double w = a == 0 ? ivs : 0.25 * ivs;
             for (int c = 0; c < 3; ++c)
                 B.gvis[(long long)(d * 9 + a * 3 + c) * mv + m] =
-                    on ? (sa[c * bL->ml.mvolume] + sb[c * bR->ml.mvolume]) * ivs : 0.0;
+                    on ? (sa[c * bL->ml.mvolume] + sb[c * bR->ml.mvolume]) * w : 0.0;
         }
     }
 }
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(256, 2) vis_face_kernel(VisBatch p)
     const long long offe = e == 0 ? 1 : B.L.sj;
     const long long offf = f == 1 ? B.L.sj : B.L.sk;
     const bool has_f = f < ndir;
-    const double mu = p.mu, kcond = p.kcond;
+    const double mu = p.mu, kcond = p.kcond, mu2 = 2.0 * p.mu, mu23 = 2.0 / 3.0 * p.mu;
     for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < mv; m += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
         if (!face_of(B, d, m, i, j, k)) continue;
@@ -156,16 +159,12 @@ __global__ void __launch_bounds__(256, 2) vis_face_kernel(VisBatch p)
             pL[q] = wv[q * sv + cL];
             pR[q] = wv[q * sv + cR];
             dxi[q] = pR[q] - pL[q];
-            // tangential central differences: (-1) then (+1)
-            double acc = -(wv[q * sv + cL - offe] + wv[q * sv + cR - offe]);
-            acc += wv[q * sv + cL + offe] + wv[q * sv + cR + offe];
-            deta[q] = 0.25 * acc;
-            dzeta[q] = 0.0;
-            if (has_f) {
-                double acc2 = -(wv[q * sv + cL - offf] + wv[q * sv + cR - offf]);
-                acc2 += wv[q * sv + cL + offf] + wv[q * sv + cR + offf];
-                dzeta[q] = 0.25 * acc2;
-            }
+            // tangential central differences, (+1) minus (-1) (their 1/4 is
+            // in the metrics)
+            deta[q] = (wv[q * sv + cL + offe] + wv[q * sv + cR + offe]) - (wv[q * sv + cL - offe] + wv[q * sv + cR - offe]);
+            dzeta[q] = has_f ? (wv[q * sv + cL + offf] + wv[q * sv + cR + offf]) -
+                                   (wv[q * sv + cL - offf] + wv[q * sv + cR - offf])
+                             : 0.0;
         }
         double gx[3][3];
 #pragma unroll
@@ -176,28 +175,30 @@ __global__ void __launch_bounds__(256, 2) vis_face_kernel(VisBatch p)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) grad[q][c] = dxi[q] * gx[0][c] + deta[q] * gx[1][c] + dzeta[q] * gx[2][c];
-        const double div = grad[0][0] + grad[1][1] + grad[2][2];
-        double tau[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                tau[a][c] = mu * (grad[a][c] + grad[c][a]) - (a == c ? 2.0 / 3.0 * mu * div : 0.0);
-        const double ub[3] = {0.5 * (pL[0] + pR[0]), 0.5 * (pL[1] + pR[1]), 0.5 * (pL[2] + pR[2])};
-        double theta[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            theta[c] = ub[0] * tau[0][c] + ub[1] * tau[1][c] + ub[2] * tau[2][c] + kcond * grad[3][c];
+            for (int c = 0; c < 3; ++c) grad[q][c] = fma(dzeta[q], gx[2][c], fma(deta[q], gx[1][c], dxi[q] * gx[0][c]));
+        // tau (symmetric: six entries) = mu (grad u + grad u^T) - 2/3 mu div u I
+        const double d23 = mu23 * (grad[0][0] + grad[1][1] + grad[2][2]);
+        const double t00 = fma(mu2, grad[0][0], -d23), t11 = fma(mu2, grad[1][1], -d23),
+                     t22 = fma(mu2, grad[2][2], -d23);
+        const double t01 = mu * (grad[0][1] + grad[1][0]), t02 = mu * (grad[0][2] + grad[2][0]),
+                     t12 = mu * (grad[1][2] + grad[2][1]);
         // the face's area vector, unit normal x area
         const double *fn = B.fn + (long long)(d * 4) * mv + m;
         const double A = fn[3 * mv];
-        const double S[3] = {fn[0] * A, fn[mv] * A, fn[2 * mv] * A};
+        const double S0 = fn[0] * A, S1 = fn[mv] * A, S2 = fn[2 * mv] * A;
         double *out = B.fvis + (long long)(d * NV) * mv + m;
+        const double r1 = fma(t02, S2, fma(t01, S1, t00 * S0));
+        const double r2 = fma(t12, S2, fma(t11, S1, t01 * S0));
+        const double r3 = fma(t22, S2, fma(t12, S1, t02 * S0));
         out[0] = 0.0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) out[(1 + a) * mv] = tau[a][0] * S[0] + tau[a][1] * S[1] + tau[a][2] * S[2];
-        out[4 * mv] = theta[0] * S[0] + theta[1] * S[1] + theta[2] * S[2];
+        out[mv] = r1;
+        out[2 * mv] = r2;
+        out[3 * mv] = r3;
+        // Theta . S = (u tau + k grad T) . S = u . (tau S) + k grad T . S
+        // (tau symmetric), u the face mean (uL + uR)/2
+        const double uts = fma(pL[2] + pR[2], r3, fma(pL[1] + pR[1], r2, (pL[0] + pR[0]) * r1));
+        const double gts = fma(grad[3][2], S2, fma(grad[3][1], S1, grad[3][0] * S0));
+        out[4 * mv] = fma(0.5, uts, kcond * gts);
     }
 }
 
