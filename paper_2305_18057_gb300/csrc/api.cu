@@ -208,7 +208,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         P.off_wv[b] = vis ? take(cur, 4 * (size_t)B.L.sv * sizeof(double)) : 0;
         P.off_rvis[b] = vis ? take(cur, (size_t)NV * d.ni * d.nj * d.nk * sizeof(double)) : 0;
         P.off_fvis[b] = vis ? take(cur, 3 * (size_t)NV * mv * sizeof(double)) : 0;
-        P.off_gvis[b] = vis ? take(cur, 27 * mv * sizeof(double)) : 0;
+        P.off_gvis[b] = vis ? take(cur, 3 * GVIS * mv * sizeof(double)) : 0;
         // two FP64 stage states, or two FP32 stage states + two FP32 increments
         P.off_stage[b] = take(cur, 2 * (size_t)B.L.elems * sizeof(double));
     }

@@ -74,6 +74,10 @@ constexpr int MAX_BLOCKS = 256;
 // state buffer slots a launch reads or writes
 enum { SLOT_USER = 0, SLOT_ST0 = 1, SLOT_ST1 = 2, SLOT_X0 = 3, SLOT_X1 = 4 };
 
+// arrays of face-gradient metrics per face family (viscous mode): grad xi_a
+// (9), the area vector (3), grad xi_a . S (3)
+constexpr int GVIS = 15;
+
 struct BlockDev {
     int ni, nj, nk;
     StateLayout L;
@@ -88,7 +92,7 @@ struct BlockDev {
     double *wv;             // viscous: (u, v, w, p / rho) of the stage input, state layout, 4 variables
     double *rvis;           // viscous: R_nu = sum over the faces of F_nu . S_out, dense interior [5][nk][nj][ni]
     double *fvis;           // viscous: F_nu . S of every face, [family * 5 + q][mvolume]
-    double *gvis;           // viscous: grad xi_a at every face, [family * 9 + a * 3 + c][mvolume]
+    double *gvis;           // viscous: face-gradient metrics, [family * GVIS + n][mvolume] (viscous.cu)
     double *st64[2];        // FP64 stage states
     float *xs[2], *ds[2];   // FP32 stage states and increments
     int tiles_i, tiles_j, kchunk, nchunks;

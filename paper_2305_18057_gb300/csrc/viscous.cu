@@ -98,12 +98,13 @@ __device__ __forceinline__ bool face_of(const BlockDev &B, int d, long long m, i
     return i < B.ni + (d == 0) && j < B.nj + (d == 1) && k < B.nk + (d == 2);
 }
 
-// grad xi_a at every d-face, a = d, e, f (the face's normal, then its two
-// tangential index directions): (Sbar_a(L) + Sbar_a(R)) / (|Omega_L| +
-// |Omega_R|), into gvis[(d * 9 + a * 3 + c) * mvolume + m]; the tangential
-// two already times the 1/4 of their central differences (exact).  Depends
-// on the boundary rules (the geometry a ghost cell carries): rerun when they
-// change.
+// The face-gradient metrics of every d-face, into gvis[(d * GVIS + n) *
+// mvolume + m]: n = 3 a + c, grad xi_a (component c) for a = d, e, f (the
+// face's normal, then its two tangential index directions), (Sbar_a(L) +
+// Sbar_a(R)) / (|Omega_L| + |Omega_R|), the tangential two already times the
+// 1/4 of their central differences (exact); n = 9 + c, the face's area
+// vector S; n = 12 + a, grad xi_a . S.  Depends on the boundary rules (the
+// geometry a ghost cell carries): rerun when they change.
 __global__ void vis_metrics_kernel(const BlockDev *blocks)
 {
     const int b = blockIdx.y, d = blockIdx.z;
@@ -120,14 +121,23 @@ __global__ void vis_metrics_kernel(const BlockDev *blocks)
         const BlockDev *bR = metric_cell(blocks, &B, Rc);
         const long long mL = mindex(bL, Lc[0], Lc[1], Lc[2]), mR = mindex(bR, Rc[0], Rc[1], Rc[2]);
         const double ivs = 1.0 / (bL->vol[mL] + bR->vol[mR]);
+        double *g = B.gvis + (long long)(d * GVIS) * mv + m;
+        const double *fn = B.fn + (long long)(d * 4) * mv + m;
+        const double A = fn[3 * mv];
+        const double S[3] = {fn[0] * A, fn[mv] * A, fn[2 * mv] * A};
+        for (int c = 0; c < 3; ++c) g[(9 + c) * mv] = S[c];
         for (int a = 0; a < 3; ++a) {
             const bool on = dirs[a] < ndir;
             const double *sa = bL->sbar + (long long)(dirs[a] * 4) * bL->ml.mvolume + mL;
             const double *sb = bR->sbar + (long long)(dirs[a] * 4) * bR->ml.mvolume + mR;
             const double w = a == 0 ? ivs : 0.25 * ivs;
-            for (int c = 0; c < 3; ++c)
-                B.gvis[(long long)(d * 9 + a * 3 + c) * mv + m] =
-                    on ? (sa[c * bL->ml.mvolume] + sb[c * bR->ml.mvolume]) * w : 0.0;
+            double gs = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double x = on ? (sa[c * bL->ml.mvolume] + sb[c * bR->ml.mvolume]) * w : 0.0;
+                g[(a * 3 + c) * mv] = x;
+                gs = fma(x, S[c], gs);
+            }
+            g[(12 + a) * mv] = gs;
         }
     }
 }
@@ -166,14 +176,16 @@ __global__ void __launch_bounds__(256, 2) vis_face_kernel(VisBatch p)
                                    (wv[q * sv + cL - offf] + wv[q * sv + cR - offf])
                              : 0.0;
         }
+        const double *g = B.gvis + (long long)(d * GVIS) * mv + m;
         double gx[3][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) gx[a][c] = B.gvis[(long long)(d * 9 + a * 3 + c) * mv + m];
-        double grad[4][3];
+            for (int c = 0; c < 3; ++c) gx[a][c] = g[(a * 3 + c) * mv];
+        // the velocity gradient (the temperature's enters only as grad T . S)
+        double grad[3][3];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 3; ++q)
 #pragma unroll
             for (int c = 0; c < 3; ++c) grad[q][c] = fma(dzeta[q], gx[2][c], fma(deta[q], gx[1][c], dxi[q] * gx[0][c]));
         // tau (symmetric: six entries) = mu (grad u + grad u^T) - 2/3 mu div u I
@@ -182,10 +194,8 @@ __global__ void __launch_bounds__(256, 2) vis_face_kernel(VisBatch p)
                      t22 = fma(mu2, grad[2][2], -d23);
         const double t01 = mu * (grad[0][1] + grad[1][0]), t02 = mu * (grad[0][2] + grad[2][0]),
                      t12 = mu * (grad[1][2] + grad[2][1]);
-        // the face's area vector, unit normal x area
-        const double *fn = B.fn + (long long)(d * 4) * mv + m;
-        const double A = fn[3 * mv];
-        const double S0 = fn[0] * A, S1 = fn[mv] * A, S2 = fn[2 * mv] * A;
+        // the face's area vector
+        const double S0 = g[9 * mv], S1 = g[10 * mv], S2 = g[11 * mv];
         double *out = B.fvis + (long long)(d * NV) * mv + m;
         const double r1 = fma(t02, S2, fma(t01, S1, t00 * S0));
         const double r2 = fma(t12, S2, fma(t11, S1, t01 * S0));
@@ -197,7 +207,7 @@ __global__ void __launch_bounds__(256, 2) vis_face_kernel(VisBatch p)
         // Theta . S = (u tau + k grad T) . S = u . (tau S) + k grad T . S
         // (tau symmetric), u the face mean (uL + uR)/2
         const double uts = fma(pL[2] + pR[2], r3, fma(pL[1] + pR[1], r2, (pL[0] + pR[0]) * r1));
-        const double gts = fma(grad[3][2], S2, fma(grad[3][1], S1, grad[3][0] * S0));
+        const double gts = fma(dzeta[3], g[14 * mv], fma(deta[3], g[13 * mv], dxi[3] * g[12 * mv]));
         out[4 * mv] = fma(0.5, uts, kcond * gts);
     }
 }
