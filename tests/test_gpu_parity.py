@@ -71,6 +71,30 @@ def test_residual_options_in_every_precision_form(precision, tol):
             assert per_var_rel(Rg[0], Ro[0]) < tol, (case, kw)
 
 
+@pytest.mark.parametrize("precision,tol", [(sensei.DF64, 1e-11), (sensei.FP32_FLUX, 2e-4), (sensei.FP32_STORE, 2e-4)])
+def test_residual_with_source_and_norms_in_every_precision_form(precision, tol):
+    """The source term, the residual norms and the conservation sums in the
+    double-float and FP32 forms (the norms of the FP32 residual, the
+    conservation sums FP64 in every form)."""
+    w = CASES["periodic3d_odd"]()
+    ni, nj, nk = w.dims[0]
+    rng = np.random.default_rng(0)
+    src = rng.normal(size=(5, nk, nj, ni)) * 1e-4
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    Ro = og.residual(Uo, src=[np.ascontiguousarray(src)])
+    g = gpu_grid(w, precision=precision)
+    Us = gpu_states(g, w)
+    R = torch.empty((5, nk, nj, ni), dtype=torch.float64, device=Us[0].device)
+    g.residual(Us, [R], [torch.as_tensor(src, device=R.device)])
+    st, l2, linf, cons = g.norms()
+    assert per_var_rel(R.cpu().numpy(), Ro[0]) < tol
+    ol2, olinf, ocons = og.norms(Ro, Uo)
+    np.testing.assert_allclose(l2, ol2, rtol=10 * tol)
+    np.testing.assert_allclose(linf, olinf, rtol=10 * tol)
+    np.testing.assert_allclose(cons, ocons, rtol=1e-13, atol=1e-13 * np.abs(ocons).max())
+
+
 def test_residual_with_source_and_norms():
     w = CASES["periodic3d_odd"]()
     ni, nj, nk = w.dims[0]
