@@ -100,7 +100,9 @@ typedef enum {
 } sensei_limiter;
 
 /* Cells of one block; nk == 1 makes the block two-dimensional (one cell
- * deep, no k-faces, rho w carried but left unchanged). */
+ * deep, no k-faces, rho w carried but left unchanged).  Every other extent
+ * is at least 2, the ghost depth (the ghost rules read up to two cells
+ * inside a face); SENSEI_ERR_INVALID_ARG otherwise. */
 typedef struct {
     int ni, nj, nk;
 } sensei_block_desc;

@@ -157,9 +157,12 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     long long tiles_total = 0;
     for (int b = 0; b < nblocks; ++b) {
         const sensei_block_desc &d = blocks[b];
-        if (d.ni < 1 || d.nj < 1 || d.nk < 1)
-            return fail(SENSEI_ERR_INVALID_ARG, "block %d: need ni, nj, nk >= 1 (got %d x %d x %d)", b, d.ni, d.nj,
-                        d.nk);
+        // every ghost rule reads up to NG cells inside a face (periodic,
+        // wall, interface), so a 3D extent is at least NG; nk == 1 is 2D
+        if (d.ni < NG || d.nj < NG || d.nk < 1 || (d.nk > 1 && d.nk < NG))
+            return fail(SENSEI_ERR_INVALID_ARG,
+                        "block %d: need ni, nj >= %d and nk >= %d or nk == 1 (got %d x %d x %d)", b, NG, NG, d.ni,
+                        d.nj, d.nk);
         if ((long long)d.ni * d.nj * d.nk > (1LL << 34))
             return fail(SENSEI_ERR_INVALID_ARG, "block %d: too many cells", b);
         if ((d.nk == 1) != P.two_d)

@@ -57,6 +57,9 @@ def test_workspace_size_grows_with_the_grid(sensei):
 def test_invalid_arguments_rejected_on_host(sensei):
     bad = [
         ([(0, 4, 4)], _scheme(sensei)),
+        ([(1, 4, 4)], _scheme(sensei)),     # below the ghost depth
+        ([(4, 1, 4)], _scheme(sensei)),
+        ([(4, 4, 0)], _scheme(sensei)),
         ([(4, 4, 4)], _scheme(sensei, gamma=1.0)),
         ([(4, 4, 4)], _scheme(sensei, limiter=7)),
         ([(4, 4, 4)], _scheme(sensei, precision=9)),
