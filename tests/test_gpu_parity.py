@@ -161,12 +161,12 @@ def test_norms_of_step_match_oracle():
     np.testing.assert_allclose(cons, ocons, rtol=1e-13)
 
 
-def test_nonphysical_state_is_reported():
-    from paper_2305_18057_gb300 import sensei
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_nonphysical_state_is_reported(precision):
     w = CASES["periodic3d_odd"]()
     U0 = [w.U0[0].copy()]
     U0[0][4, 3, 5, 7] = 0.0          # rho e_t = 0: negative pressure in one cell
-    g = gpu_grid(w)
+    g = gpu_grid(w, precision=precision)
     Us = gpu_states(g, w, U0)
     g.rk_step(Us, RK["rk3"], dt=1e-6)
     st, *_ = g.norms(check=False)
