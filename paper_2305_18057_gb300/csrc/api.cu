@@ -580,8 +580,10 @@ sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, doub
     const long long nitems = total_items(grid->plan.blocks);
     if (cfl > 0.0) {
         CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
+        int kchunk = 1;
+        for (const HostBlock &H : grid->plan.blocks) kchunk = std::max(kchunk, H.dev.kchunk);
         CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, local ? 1 : 0,
-                           cfl, grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms),
+                           cfl, grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms), kchunk,
                            grid->scheme.precision == SENSEI_FP32_FLUX || grid->scheme.precision == SENSEI_FP32_STORE,
                            viscous_dt_factor(grid), s));
         grid->kernel_launches++;

@@ -71,8 +71,10 @@ struct DtMath<float> {
     static __device__ __forceinline__ float vol(const BlockDev &B, long long m) { return B.vol32[m]; }
 };
 
-// One CTA per work item (tile column x k-chunk of one block), grid-stride
-// over the items; each thread walks its column.
+// The stencil's work items (tile column x k-chunk of one block), grid-stride
+// in x, each item's k-chunk split into pieces of DT_SUB planes along y, so
+// that no thread walks a long column alone; each thread walks its piece.
+constexpr int DT_SUB = 16;
 template <typename R>
 __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, int nblocks, long long nitems,
                                                       const __grid_constant__ DtUser user, double gamma,
@@ -95,7 +97,8 @@ __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, in
         const int chunk = (int)(rest / B.tiles_j);
         const int i = tile_i * TI + ti, j = tile_j * TJ + tj;
         if (i >= B.ni || j >= B.nj) continue;
-        const int k0 = chunk * B.kchunk, k1 = min(k0 + B.kchunk, B.nk);
+        const int k0 = chunk * B.kchunk + (int)blockIdx.y * DT_SUB;
+        const int k1 = min(min(k0 + DT_SUB, chunk * B.kchunk + B.kchunk), B.nk);
         const int ndir = B.nk == 1 ? 2 : 3;
         const double *U = user.u[b];
         const long long mv = B.ml.mvolume;
@@ -172,11 +175,12 @@ __global__ void norms_finalize_kernel(const double *__restrict__ partials, int n
 }  // namespace
 
 cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
-                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, bool fp32,
-                      double vfac, cudaStream_t s)
+                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid_x, int kchunk,
+                      bool fp32, double vfac, cudaStream_t s)
 {
     DtUser u;
     for (int b = 0; b < nblocks; ++b) u.u[b] = user[b];
+    const dim3 grid((unsigned)grid_x, (unsigned)((kchunk + DT_SUB - 1) / DT_SUB));
     if (fp32)
         dt_kernel<float><<<grid, NTHREADS, 0, s>>>(blocks, nblocks, nitems, u, gamma, local, cfl, dt_bits, err, 0.0);
     else

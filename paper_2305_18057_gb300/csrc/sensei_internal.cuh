@@ -199,8 +199,8 @@ int stencil_ctas_per_sm_f32s(int limiter, bool two_d);
 // fp32: FP32 arithmetic on the FP32 metric copies (the mixed-precision modes);
 // vfac = 4 max(4/3, gamma) mu / Pr adds the viscous bound vfac |Sbar_d|^2 / (rho |Omega|)
 cudaError_t launch_dt(const BlockDev *blocks, int nblocks, long long nitems, double *const *user, double gamma,
-                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid, bool fp32,
-                      double vfac, cudaStream_t s);
+                      int local, double cfl, unsigned long long *dt_bits, unsigned *err, int grid_x, int kchunk,
+                      bool fp32, double vfac, cudaStream_t s);
 // the face gradient metrics B.gvis of every block (after the descriptors
 // with the boundary rules are on the device); max_faces: the largest mvolume
 cudaError_t launch_vis_metrics(const BlockDev *blocks, int nblocks, long long max_faces, cudaStream_t s);
