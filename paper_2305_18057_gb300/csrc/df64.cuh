@@ -101,6 +101,35 @@ __host__ __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c)
     return df64(s, e);
 }
 
+// Sums of products a1 b1 + a2 b2 + ... accumulated in one unnormalised pair:
+// each product's exact error and each sum's rounding error gather in the
+// correction term, renormalised once at the end.
+struct df64_acc {
+    float s, e;
+};
+__host__ __device__ __forceinline__ df64_acc acc_mul(df64 a, df64 b)
+{
+    const float p = a.hi * b.hi;
+    float pe = df_fma(a.hi, b.hi, -p);
+    pe = df_fma(a.hi, b.lo, df_fma(a.lo, b.hi, pe));
+    return df64_acc{p, pe};
+}
+__host__ __device__ __forceinline__ df64_acc acc_fma(df64 a, df64 b, df64_acc x)
+{
+    const float p = a.hi * b.hi;
+    float pe = df_fma(a.hi, b.hi, -p);
+    pe = df_fma(a.hi, b.lo, df_fma(a.lo, b.hi, pe));
+    float s, e;
+    two_sum(x.s, p, s, e);
+    return df64_acc{s, x.e + (e + pe)};
+}
+__host__ __device__ __forceinline__ df64 acc_done(df64_acc x)
+{
+    float s, e;
+    fast_two_sum(x.s, x.e, s, e);
+    return df64(s, e);
+}
+
 // Newton refinement of the single-precision reciprocal: r' = r + r (1 - a r)
 __host__ __device__ __forceinline__ df64 rcp_df(df64 a)
 {

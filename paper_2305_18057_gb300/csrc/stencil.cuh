@@ -300,6 +300,31 @@ __device__ __forceinline__ void face_states(R wm, R w0, R wp, R c1, R c2, R half
     }
 }
 
+// a1 b1 + a2 b2 + a3 b3 (+ a4 b4 + a5 b5) as a chain of fused multiply-adds
+// (FP64 and FP32), or in the double-float form as one accumulation with a
+// single renormalisation
+template <typename R>
+__device__ __forceinline__ R dot3(R a1, R b1, R a2, R b2, R a3, R b3)
+{
+    return fma(a3, b3, fma(a2, b2, a1 * b1));
+}
+template <>
+__device__ __forceinline__ df64 dot3<df64>(df64 a1, df64 b1, df64 a2, df64 b2, df64 a3, df64 b3)
+{
+    return acc_done(acc_fma(a3, b3, acc_fma(a2, b2, acc_mul(a1, b1))));
+}
+template <typename R>
+__device__ __forceinline__ R dot5(R a1, R b1, R a2, R b2, R a3, R b3, R a4, R b4, R a5, R b5)
+{
+    return fma(a5, b5, fma(a4, b4, fma(a3, b3, fma(a2, b2, a1 * b1))));
+}
+template <>
+__device__ __forceinline__ df64 dot5<df64>(df64 a1, df64 b1, df64 a2, df64 b2, df64 a3, df64 b3, df64 a4, df64 b4,
+                                           df64 a5, df64 b5)
+{
+    return acc_done(acc_fma(a5, b5, acc_fma(a4, b4, acc_fma(a3, b3, acc_fma(a2, b2, acc_mul(a1, b1))))));
+}
+
 // Roe flux through a face of unit normal n and area A between primitive
 // states wl, wr: A/2 [F(wl) + F(wr) - sum_k |lam_k| alpha_k r_k], three-wave
 // form, Harten's entropy fix on the acoustic waves (delta = fix * a).
@@ -315,17 +340,17 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     const R rr = wr[0], ur = wr[1], vr = wr[2], zr = wr[3], pr = wr[4];
     // products and sums as explicit fused multiply-adds (FP64 contracts them
     // anyway; double-float forms each in one operation)
-    const R vnl = fma(nz, zl, fma(ny, vl, nx * ul));
-    const R vnr = fma(nz, zr, fma(ny, vr, nx * ur));
-    const R rhl = fma(half_pos(rl), fma(zl, zl, fma(vl, vl, ul * ul)), kg * pl);   // rho h_t
-    const R rhr = fma(half_pos(rr), fma(zr, zr, fma(vr, vr, ur * ur)), kg * pr);
+    const R vnl = dot3(nx, ul, ny, vl, nz, zl);
+    const R vnr = dot3(nx, ur, ny, vr, nz, zr);
+    const R rhl = fma(half_pos(rl), dot3(ul, ul, vl, vl, zl, zl), kg * pl);   // rho h_t
+    const R rhr = fma(half_pos(rr), dot3(ur, ur, vr, vr, zr, zr), kg * pr);
     const R ml = rl * vnl, mr = rr * vnr;
     const R psum = pl + pr;
     R c[NV];
     c[0] = ml + mr;
-    c[1] = fma(nx, psum, fma(mr, ur, ml * ul));
-    c[2] = fma(ny, psum, fma(mr, vr, ml * vl));
-    c[3] = fma(nz, psum, fma(mr, zr, ml * zl));
+    c[1] = dot3(ml, ul, mr, ur, nx, psum);
+    c[2] = dot3(ml, vl, mr, vr, ny, psum);
+    c[3] = dot3(ml, zl, mr, zr, nz, psum);
     c[4] = fma(rhr, vnr, rhl * vnl);
     // Roe average with weights sqrt(rho): with q = 1/sqrt(rl rr) and
     // t = sqrt(rr/rl) = rr q, phi = (phi_l + t phi_r)/(1+t), the averaged
@@ -339,13 +364,13 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     const R u = wL * fma(t, ur, ul), v = wL * fma(t, vr, vl), w = wL * fma(t, zr, zl);
     const R H = wL * (fma(t * rhr, rl, rhl * rr) * (qq * qq));
     const R rho = rlr * qq;
-    const R q2 = fma(w, w, fma(v, v, u * u));
+    const R q2 = dot3(u, u, v, v, w, w);
     const R hq2 = R(0.5) * q2;
     const R a2 = gm1 * (H - hq2);
     const R ia = rsqrt1_t(a2);
     const R a = a2 * ia;
     const R ia2 = ia * ia;
-    const R vn = fma(nz, w, fma(ny, v, nx * u));
+    const R vn = dot3(nx, u, ny, v, nz, w);
     const R dr = rr - rl, dp = pr - pl, du = ur - ul, dv = vr - vl, dw = zr - zl, dvn = vnr - vnl;
     R l1 = abs_bits(vn - a), l3 = abs_bits(vn + a);
     R l2 = abs_bits(vn);
@@ -368,10 +393,10 @@ __device__ __forceinline__ void roe_flux(const R wl[NV], const R wr[NV], R nx, R
     const R s13 = c1w + c3w, d13 = c3w - c1w;
     const R D0 = s13 + c2w;
     const R g = fma(a, d13, -(cs * dvn));
-    const R D1 = fma(cs, du, fma(nx, g, u * D0));
-    const R D2 = fma(cs, dv, fma(ny, g, v * D0));
-    const R D3 = fma(cs, dw, fma(nz, g, w * D0));
-    const R D4 = fma(-hq2, c2w, fma(H - q2, s13, fma(w, D3, fma(v, D2, u * D1))));
+    const R D1 = dot3(u, D0, nx, g, cs, du);
+    const R D2 = dot3(v, D0, ny, g, cs, dv);
+    const R D3 = dot3(w, D0, nz, g, cs, dw);
+    const R D4 = dot5(u, D1, v, D2, w, D3, H - q2, s13, -hq2, c2w);
     F[0] = fma(h, c[0], -D0);
     F[1] = fma(h, c[1], -D1);
     F[2] = fma(h, c[2], -D2);
