@@ -81,7 +81,7 @@ def test_periodic3d_256_full_residual_dt_and_graph_step():
     # FP64: 1e-11.  Double-float carries 48 bits (unit roundoff 2^-48, 32
     # times FP64's), and on this smooth 256^3 field the residual is ~1e-3 of
     # the face fluxes it is the difference of, so its bar is the FP64 bar
-    # scaled by the roundoff ratio: 32e-11 (measured 4.1e-11; FP64 1.3e-12)
+    # scaled by the roundoff ratio: 32e-11 (measured 4.2e-11; FP64 1.3e-12)
     for precision, tol in ((sensei.FP64, 1e-11), (sensei.DF64, 32e-11)):
         g, Us = _tuned(w, precision)
         R = _residual(g, w, Us)[0].cpu().numpy()
