@@ -8,8 +8,9 @@
 // two-sum (the exact rounding error of a + b), Dekker's fast two-sum (for
 // |a| >= |b|), the two-product through a fused multiply-add (the exact error
 // of a * b), and Newton's iteration for the reciprocal and the reciprocal
-// square root from the single-precision approximations.  Host and device
-// share the code (the host forms the launch constants).
+// square root from the single-precision approximations.  A multiply-add
+// and a sum of products are formed with a single renormalisation.  Host and
+// device share the code (the host forms the launch constants).
 #pragma once
 
 #include <math.h>
