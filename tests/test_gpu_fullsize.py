@@ -15,7 +15,8 @@ bench times (the autotuned schedule; steps as CUDA-graph replays):
     against the oracle's (1e-11 of the sampled residual's scale); one
     FP32-storage graph step within density L2 1e-5 of the FP64 step;
   Navier-Stokes at 256^3: the viscous residual on sampled sub-box cores
-    (1e-11).
+    (1e-11);
+  conservation on the periodic 256^3 grid over 50 graph steps, all forms.
 The mixed forms are held to their bar against the FP64 path, which the same
 test first holds to the oracle.
 """
@@ -242,3 +243,29 @@ def test_navier_stokes_256_residual_on_sampled_subbox_cores():
     err = per_var_rel(got_all, want_all)
     print(f"Navier-Stokes 256^3 residual on sub-box cores: {err:.3g} of the oracle's")
     assert err < 1e-11
+
+
+@pytest.mark.parametrize("precision,tol", [(sensei.FP64, 1e-12), (sensei.DF64, 1e-12), (sensei.FP32_FLUX, 1e-12),
+                                           (sensei.FP32_STORE, 1e-10)])
+def test_periodic3d_256_conserves_over_50_graph_steps(precision, tol):
+    """A property that holds at any size: on the fully periodic 256^3 grid
+    every face flux leaves one cell and enters the other, so the sums of
+    |Omega| U (mass, momentum, energy) stay constant; after 50 SSPRK3 steps
+    replayed from a graph they agree with the initial sums to round-off (the
+    FP32-storage form at the level of its FP32 increments)."""
+    w = wl.periodic_3d(n=256)
+    g, Us = _tuned(w, precision)
+    graph = g.step_graph(Us, sensei.RK3_SSP, cfl=0.5)
+    graph.launch()
+    torch.cuda.synchronize()
+    cons0 = g.norms()[3]
+    for _ in range(50):
+        graph.launch()
+    torch.cuda.synchronize()
+    cons1 = g.norms()[3]
+    graph.close()
+    # each component against the largest (the momenta may sum to ~0)
+    scale = np.abs(cons0).max()
+    assert np.abs(np.asarray(cons1) - np.asarray(cons0)).max() <= tol * scale, (precision, cons0, cons1)
+    del g, Us
+    _free()
