@@ -269,3 +269,26 @@ def test_periodic3d_256_conserves_over_50_graph_steps(precision, tol):
     assert np.abs(np.asarray(cons1) - np.asarray(cons0)).max() <= tol * scale, (precision, cons0, cons1)
     del g, Us
     _free()
+
+
+@pytest.mark.parametrize("precision,tol", [(sensei.FP64, 1e-12), (sensei.DF64, 32e-12), (sensei.FP32_FLUX, 1e-6)])
+def test_periodic3d_256_preserves_a_uniform_state(precision, tol):
+    """A property that holds at any size: the area vectors of every closed
+    cell sum to zero, so on the curvilinear 256^3 map a uniform state has a
+    zero residual up to the rounding of the face fluxes (bounded against a
+    face flux, (rho |u|^2 + p) h^2)."""
+    import dataclasses
+    w = wl.periodic_3d(n=256)
+    U = w.U0[0]
+    ubar = np.array([float(np.mean(U[v])) for v in range(5)])
+    Uu = np.broadcast_to(ubar[:, None, None, None], U.shape).copy()
+    w = dataclasses.replace(w, U0=[Uu])
+    g, Us = _tuned(w, precision)
+    R = _residual(g, w, Us)[0]
+    rmax = float(R.abs().max())
+    del R, g, Us
+    _free()
+    rho, m2, E = ubar[0], float(np.sum(ubar[1:4] ** 2)), ubar[4]
+    p = (w.gamma - 1.0) * (E - 0.5 * m2 / rho)
+    flux = (m2 / rho + p) * (1.0 / 256) ** 2
+    assert rmax <= tol * flux, (precision, rmax, flux)
