@@ -438,7 +438,7 @@ def main():
             "traffic": None if two_d else MEASURED_TRAFFIC_B_PER_CELL["fp32_flux"] * cells,
             "traffic_source": "ncu DRAM bytes per cell of the 192^3 capture x cells (3-stage average)",
             "peak_source": peak_src,
-            "kernel": "stencil_kernel<float,double> (FP32 MUSCL + Roe on the FP64 state, FP64 update)",
+            "kernel": "stencil32_kernel<double> (FP32 MUSCL + Roe on the FP64 state, FP64 update)",
             "alg_bytes_per_launch": byts, "kernel_ms_per_launch": per_launch_ms,
         }
 
