@@ -231,7 +231,7 @@ sensei_status sensei_norms(sensei_grid *grid, double *l2, double *linf, double *
 /* A CUDA graph of one sensei_rk_step (same arguments, fixed pointers),
  * replayed by sensei_step_graph_launch on any stream.  With a captured step a
  * whole SSPRK3 step of any number of blocks is one graph launch of six
- * kernels: ghost fill, dt reduction, three persistent stencil launches,
+ * kernels: ghost fill, dt reduction, three batched stencil launches,
  * norm finalisation.  Creation synchronises `stream` and captures on a
  * private stream (graph instantiation is done by the CUDA driver).  A graph
  * refuses to launch (SENSEI_ERR_STATE) once boundary rules or the schedule of
@@ -242,7 +242,7 @@ sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int 
 sensei_status sensei_step_graph_launch(sensei_step_graph *graph, sensei_stream stream);
 sensei_status sensei_step_graph_destroy(sensei_step_graph *graph);
 
-/* Pick the work schedule of the persistent stencil launches by timing them
+/* Pick the work schedule of the batched stencil launches by timing them
  * on this grid and the states U (dt = 0 first-stage launches into the stage
  * buffers; U's ghosts are refilled, its interior untouched): the k-extent of
  * a work item (tile of 32 x 8 cells x kchunk planes) and persistent CTAs
