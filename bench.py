@@ -128,6 +128,40 @@ def fp64_peak_tflops(sm_mhz=2070.0):
     return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
 
 
+# FP32 vector peak derived the same way: 152 SMs x 128 FP32 FMA lanes per SM
+# per clock x 2 flops x clock (80.5 TFLOP/s at 2070 MHz).
+def fp32_peak_tflops(sm_mhz=2070.0):
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def step_flops_per_launch(limiter, two_d, cells, stages=3):
+    """Formula flops of one stencil launch, averaged over the stages of an
+    SSPRK3 step (the first accumulates the norm partials, the others blend
+    U^n)."""
+    return cells * (alg_flops_per_cell(limiter, two_d, False, True)
+                    + alg_flops_per_cell(limiter, two_d, True, False) * (stages - 1)) / stages
+
+
+def pipe_roofline(form, flops_per_launch, ms_per_launch):
+    """The arithmetic side of a stencil launch's roofline: formula flops per
+    mean launch time against the vector peak of the pipe that carries the
+    reconstruction and the Roe flux -- FP64 for fp64; FP32 for the FP32 forms;
+    for double-float (the FP64 formula carried as pairs of FP32 numbers on
+    the FP32 pipe) the FP64 peak, so that a fraction above 1 is the factor by
+    which it passes the native FP64 roof."""
+    tf = flops_per_launch / (ms_per_launch / 1e3) / 1e12
+    if form in ("fp32_flux", "fp32_store"):
+        peak = fp32_peak_tflops(2070.0)
+        src = "derived FP32 vector peak: 152 SMs x 128 FMA/clk x 2 flop x 2070 MHz"
+    else:
+        peak = fp64_peak_tflops(2070.0)
+        src = "derived FP64 vector peak: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz"
+        if form == "df64":
+            src += " (double-float carries the FP64 formula on the FP32 pipe)"
+    return {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+            "peak_source": src, "alg_flops_per_launch": flops_per_launch}
+
+
 # ------------------------------------------------------------------ clocks --
 
 class ClockSampler:
@@ -415,8 +449,7 @@ def main():
     byts = cells * sum(alg_bytes_per_cell(form, s_, two_d) for s_ in range(stages)) / stages
     hbm_gbs = byts / (per_launch_ms / 1e3) / 1e9
     if main_prec == sensei.FP64:
-        flops = cells * (alg_flops_per_cell(w.limiter, two_d, False, True)
-                         + alg_flops_per_cell(w.limiter, two_d, True, False) * 2) / 3.0
+        flops = step_flops_per_launch(w.limiter, two_d, cells, stages)
         fp64_peak = fp64_peak_tflops(2070.0)
         achieved_tf = flops / (per_launch_ms / 1e3) / 1e12
         roofline = {
@@ -440,6 +473,7 @@ def main():
             "peak_source": peak_src,
             "kernel": "stencil32_kernel<double> (FP32 MUSCL + Roe on the FP64 state, FP64 update)",
             "alg_bytes_per_launch": byts, "kernel_ms_per_launch": per_launch_ms,
+            "pipe": pipe_roofline(form, step_flops_per_launch(w.limiter, two_d, cells, stages), per_launch_ms),
         }
 
     line = {
@@ -516,7 +550,9 @@ def main():
                 "rho_l2_rel_err_vs_fp64": rho_l2, "steps_compared": n_cmp,
                 "roofline": {"bound": "hbm", "achieved": bv / (stv / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": bv / (stv / 1e3) / 1e9 / peaks["hbm_gbs"],
-                             "kernel_ms_per_launch": stv, "alg_bytes_per_launch": bv, "peak_source": peak_src}}
+                             "kernel_ms_per_launch": stv, "alg_bytes_per_launch": bv, "peak_source": peak_src,
+                             "pipe": pipe_roofline(vname, step_flops_per_launch(w.limiter, two_d, cells, stages),
+                                                   stv)}}
             del gv, Uv
         del g64, U64
         # the Navier-Stokes form (NEXT row f2) in FP64 on the same grid and
