@@ -57,7 +57,7 @@ typedef enum {
     SENSEI_ERR_INVALID_ARG = 1,   /* bad pointer, size, enum, block/face index or layout */
     SENSEI_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the CUDA error) */
     SENSEI_ERR_NONPHYSICAL = 3,   /* a kernel met rho <= 0, p <= 0 or a non-finite value */
-    SENSEI_ERR_TIMEOUT = 4,       /* reserved: a bounded device wait gave up */
+    SENSEI_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (the FP32 stencil's tile copies; reported by sensei_norms) */
     SENSEI_ERR_UNSUPPORTED = 5,   /* valid request this build does not implement */
     SENSEI_ERR_STATE = 6          /* call out of order (e.g. a boundary face left unset) */
 } sensei_status;
