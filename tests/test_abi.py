@@ -73,10 +73,12 @@ def test_invalid_arguments_rejected_on_host(sensei):
             sensei.sensei_workspace_size(blocks, sch)
         assert e.value.status == sensei.ERR_INVALID_ARG
         assert sensei.sensei_last_error() != ""
-    # the viscous flux is FP64 only
-    with pytest.raises(sensei.SenseiError) as e:
-        sensei.sensei_workspace_size([(4, 4, 4)], _scheme(sensei, mu=1e-3, prandtl=0.72, precision=sensei.FP32_FLUX))
-    assert e.value.status == sensei.ERR_UNSUPPORTED
+    # the viscous flux runs in the FP64 and double-float forms only
+    for prec in (sensei.FP32_FLUX, sensei.FP32_STORE):
+        with pytest.raises(sensei.SenseiError) as e:
+            sensei.sensei_workspace_size([(4, 4, 4)], _scheme(sensei, mu=1e-3, prandtl=0.72, precision=prec))
+        assert e.value.status == sensei.ERR_UNSUPPORTED
+    assert sensei.sensei_workspace_size([(4, 4, 4)], _scheme(sensei, mu=1e-3, prandtl=0.72, precision=sensei.DF64)) > 0
     # its workspace adds the primitives and the viscous residual
     assert sensei.sensei_workspace_size([(32, 16, 8)], _scheme(sensei, mu=1e-3, prandtl=0.72)) > \
         sensei.sensei_workspace_size([(32, 16, 8)], _scheme(sensei))
