@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, in
             const R a = a2 * M::rsqrt(a2);
             const long long m = k * B.ml.mplane + j * B.ml.mpitch + i;
             R sum = R(0);
-            // viscous bound per direction: vfac / rho |Sbar_d|^2 / |Omega| (FP64 only)
+            // viscous bound per direction: vfac / rho |Sbar_d|^2 / |Omega| (the FP64 time step of the FP64 and double-float forms)
             const double vr = vfac > 0.0 ? vfac * (double)ir * B.ivol[m] : 0.0;
             for (int d = 0; d < ndir; ++d) {
                 const long long q = (long long)(d * 4) * mv + m;
