@@ -24,7 +24,9 @@
  *   - All state, residual, node and source arrays are CALLER-OWNED device
  *     memory.  The library never allocates device memory: its scratch
  *     (metrics, Runge-Kutta stage buffers, reduction partials) lives in a
- *     caller-allocated workspace handed to sensei_create_grid.
+ *     caller-allocated workspace handed to sensei_create_grid.  The one
+ *     exception is sensei_residual_norms_noalloc, whose scratch is a static
+ *     164 KB array in the library's own device memory (below).
  *   - Pointer arrays ("one per block") are HOST arrays of DEVICE pointers.
  *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
  *     legacy default stream) except sensei_norms, which synchronises it.
@@ -272,15 +274,19 @@ sensei_status sensei_profile_read(sensei_grid *grid, double *stencil_ms, long lo
  * It needs no grid and no workspace.  R is a dense device array
  * R[5][nk][nj][ni] (the layout sensei_residual writes); l2 and linf (host,
  * 5 doubles each, either may be NULL) receive sqrt(sum R_q^2 / N) and
- * max |R_q| over the N = ni*nj*nk cells.  Synchronises `stream`.
+ * max |R_q| over the N = ni*nj*nk cells; a NaN entry of R_q makes both
+ * norms of q NaN (the maxima propagate it).  Synchronises `stream`: the
+ * norms are read back to the host before the call returns.
  * Scratch: a fixed 164 KB array in the library's own device memory, held by
  * every GPU that loads the library until the process exits; N above
  * 8,388,608 cells is rejected with SENSEI_ERR_INVALID_ARG.  The first call on
- * a device looks up that array's address (once per device, with the device
- * current); make that first call before any stream capture.  All calls share
- * the array and it keeps the last call's contents (each call overwrites every
- * slot it reads), so calls that overlap on the GPU, from different streams
- * or threads, race: serialise them. */
+ * a device does a one-time set-up: it looks up that array's address (with
+ * the device current) and keeps it; make that first call before any stream
+ * capture begins, and do not call the entry point again on a device after a
+ * cudaDeviceReset of it (the kept address belongs to the old context).  All
+ * calls share the array and it keeps the last call's contents (each call
+ * overwrites every slot it reads), so calls that overlap on the GPU, from
+ * different streams or threads, race: serialise them. */
 sensei_status sensei_residual_norms_noalloc(const double *R, int ni, int nj, int nk, double *l2, double *linf,
                                             sensei_stream stream);
 

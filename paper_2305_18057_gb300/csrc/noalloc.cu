@@ -13,7 +13,13 @@
 // library holds it (164 KB) until the process exits.  In host code its name
 // is only a stand-in, not a device address, so the address is looked up once
 // per device with cudaGetSymbolAddress, with that device current, the first
-// time the entry point runs on it.
+// time the entry point runs on it.  The cached address belongs to the
+// device's context at that time: after a cudaDeviceReset of that device the
+// entry point must not be called again in the same process.
+//
+// A non-finite residual entry is not hidden: the sums of squares carry it
+// into L2, and the maxima propagate NaN (fmax alone would drop it), so a NaN
+// anywhere in R_q makes both norms of variable q NaN.
 #include <mutex>
 
 #include "sensei_internal.cuh"
@@ -32,6 +38,9 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_norm_scratch[kMaxParts * kQ + 2 * NV];
 
 std::mutex g_setup_mutex;
+
+// max(a, b) that returns NaN when either operand is NaN
+__device__ __forceinline__ double nan_max(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
 double *g_scratch_addr[kMaxDevices] = {};
 
 // CTA b reduces the cells [b*chunk, (b+1)*chunk) of every variable of the
@@ -48,11 +57,11 @@ __global__ void noalloc_partials(const double *__restrict__ R, long long n, long
         for (long long c = lo + threadIdx.x; c < hi; c += kThreads) {
             double r = R[v * n + c];
             s2 += r * r;
-            mx = fmax(mx, fabs(r));
+            mx = nan_max(mx, fabs(r));
         }
         for (int o = 16; o > 0; o >>= 1) {
             s2 += __shfl_down_sync(0xffffffffu, s2, o);
-            mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            mx = nan_max(mx, __shfl_down_sync(0xffffffffu, mx, o));
         }
         if ((threadIdx.x & 31) == 0) {
             red[v][threadIdx.x >> 5] = s2;
@@ -63,7 +72,7 @@ __global__ void noalloc_partials(const double *__restrict__ R, long long n, long
     if (threadIdx.x < kQ) {
         double acc = 0.0;
         for (int w = 0; w < kThreads / 32; ++w)
-            acc = threadIdx.x < NV ? acc + red[threadIdx.x][w] : fmax(acc, red[threadIdx.x][w]);
+            acc = threadIdx.x < NV ? acc + red[threadIdx.x][w] : nan_max(acc, red[threadIdx.x][w]);
         scratch[(long long)blockIdx.x * kQ + threadIdx.x] = acc;
     }
 }
@@ -76,11 +85,11 @@ __global__ void noalloc_finalize(double *scratch, int nparts, long long n)
     double acc = 0.0;
     for (int p = lane; p < nparts; p += 32) {
         double x = scratch[(long long)p * kQ + q];
-        acc = q < NV ? acc + x : fmax(acc, x);
+        acc = q < NV ? acc + x : nan_max(acc, x);
     }
     for (int o = 16; o > 0; o >>= 1) {
         double y = __shfl_down_sync(0xffffffffu, acc, o);
-        acc = q < NV ? acc + y : fmax(acc, y);
+        acc = q < NV ? acc + y : nan_max(acc, y);
     }
     if (lane == 0) scratch[kMaxParts * kQ + q] = q < NV ? sqrt(acc / (double)n) : acc;
 }
