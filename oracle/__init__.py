@@ -55,9 +55,14 @@ def build(force: bool = False, counting: bool = False) -> str:
         cmd = ["g++", "-O2", "-std=c++17", "-fpermissive", "-w", "-ffp-contract=off", "-fPIC", "-shared",
                "-o", tmp, OPCOUNT_SRC, "-lm"]
     else:
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp",
                "-o", tmp, SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    if counting:
+        subprocess.run(cmd, check=True)
+    elif subprocess.run(cmd, capture_output=True).returncode != 0:
+        # a host compiler without OpenMP: the same source, one thread
+        cmd.remove("-fopenmp")
+        subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
 
@@ -94,11 +99,21 @@ def lib(counting: bool = False):
             L.ora_psi.argtypes = [C.c_int, C.c_double]
             L.ora_cons_to_prim.argtypes = [C.c_double, _dp, _dp]
             L.ora_prim_to_cons.argtypes = [C.c_double, _dp, _dp]
+            L.ora_set_threads.restype = C.c_int
+            L.ora_set_threads.argtypes = [C.c_int]
+            L.ora_set_threads(1)
             if counting:
                 L.ora_opcount_reset.argtypes = []
                 L.ora_opcount_get.argtypes = [C.POINTER(C.c_ulonglong)]
             _libs[counting] = L
     return _libs[counting]
+
+
+def set_threads(n: int) -> int:
+    """Host threads for the oracle's loops over k-planes (results are bitwise
+    the same for every count); returns the count in effect (1 without
+    OpenMP)."""
+    return lib().ora_set_threads(int(n))
 
 
 OPCOUNT_KINDS = ("add", "mul", "div", "sqrt", "cmp", "abs", "neg")

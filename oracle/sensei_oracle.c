@@ -25,6 +25,14 @@
  * A 2D block is a one-cell-deep slab (nk == 1); it has f = 4 faces per cell
  * (Eq. residual), so its k-faces are never used.
  *
+ * Threads: built with OpenMP, the loops over k-planes whose iterations are
+ * independent (every face flux, the per-cell sums of Eq. residual, the
+ * Runge-Kutta stage and final updates, the local time steps) may run on
+ * several host threads (ora_set_threads; 1 by default).  Each iteration
+ * computes the same values in the same order whatever the thread count;
+ * the reductions (norms, the global time-step minimum) stay serial, so the
+ * results are bitwise independent of the thread count.
+ *
  * Parity status: every routine here is pinned by a CPU test (closed forms,
  * invariants, exact Riemann and oblique-shock solutions, brute force); see
  * tests/test_oracle_*.py.
@@ -32,6 +40,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define NV 5   /* rho, rho*u, rho*v, rho*w, rho*e_t  (Eq. governing, vector Q) */
 #define NG 2   /* ghost layers: the MUSCL stencil of Eq. flux reaches i-1..i+2 */
@@ -720,13 +731,14 @@ static void block_residual(const ora_grid *g, int bi, double *const *U, double *
     double *Fi = calloc((size_t)NV * nfi, sizeof(double));
     double *Fj = calloc((size_t)NV * nfj, sizeof(double));
     double *Fk = is2d(b) ? NULL : calloc((size_t)NV * nfk, sizeof(double));
-    double S[3], F[NV];
-    long c[4];
 
     /* every face flux once */
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < b->nk; ++k)
         for (int j = 0; j < b->nj; ++j)
             for (int i = 0; i <= b->ni; ++i) {
+                double S[3], F[NV];
+                long c[4];
                 for (int m = 0; m < 4; ++m) c[m] = cell(b, i - 2 + m, j, k);
                 for (int a = 0; a < 3; ++a) S[a] = b->Si[a * nfi + fi_index(b, i, j, k)];
                 stencil_flux(g, b, u, c, S, F);
@@ -737,9 +749,12 @@ static void block_residual(const ora_grid *g, int bi, double *const *U, double *
                 }
                 for (int q = 0; q < NV; ++q) Fi[q * nfi + fi_index(b, i, j, k)] = F[q];
             }
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < b->nk; ++k)
         for (int j = 0; j <= b->nj; ++j)
             for (int i = 0; i < b->ni; ++i) {
+                double S[3], F[NV];
+                long c[4];
                 for (int m = 0; m < 4; ++m) c[m] = cell(b, i, j - 2 + m, k);
                 for (int a = 0; a < 3; ++a) S[a] = b->Sj[a * nfj + fj_index(b, i, j, k)];
                 stencil_flux(g, b, u, c, S, F);
@@ -750,10 +765,13 @@ static void block_residual(const ora_grid *g, int bi, double *const *U, double *
                 }
                 for (int q = 0; q < NV; ++q) Fj[q * nfj + fj_index(b, i, j, k)] = F[q];
             }
-    if (!is2d(b))
+    if (!is2d(b)) {
+#pragma omp parallel for schedule(static)
         for (int k = 0; k <= b->nk; ++k)
             for (int j = 0; j < b->nj; ++j)
                 for (int i = 0; i < b->ni; ++i) {
+                    double S[3], F[NV];
+                    long c[4];
                     for (int m = 0; m < 4; ++m) c[m] = cell(b, i, j, k - 2 + m);
                     for (int a = 0; a < 3; ++a) S[a] = b->Sk[a * nfk + fk_index(b, i, j, k)];
                     stencil_flux(g, b, u, c, S, F);
@@ -764,10 +782,12 @@ static void block_residual(const ora_grid *g, int bi, double *const *U, double *
                     }
                     for (int q = 0; q < NV; ++q) Fk[q * nfk + fk_index(b, i, j, k)] = F[q];
                 }
+    }
 
     /* sum over the faces of each cell with the outward sign:
      * (F_{i+1/2} - F_{i-1/2}) + (F_{j+1/2} - F_{j-1/2}) + (F_{k+1/2} - F_{k-1/2}) - |Omega| S */
     long nint = n_interior(b);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < b->nk; ++k)
         for (int j = 0; j < b->nj; ++j)
             for (int i = 0; i < b->ni; ++i) {
@@ -1115,11 +1135,13 @@ static double rk_step_impl(const ora_grid *g, double *const *U, const double *co
     for (int bi = 0; bi < nb; ++bi) {
         const ora_block *b = &g->b[bi];
         dtc[bi] = malloc(sizeof(double) * n_interior(b));
-        if (local)
+        if (local) {
+#pragma omp parallel for schedule(static)
             for (int k = 0; k < b->nk; ++k)
                 for (int j = 0; j < b->nj; ++j)
                     for (int ii = 0; ii < b->ni; ++ii)
                         dtc[bi][interior(b, ii, j, k)] = cell_dt(g, b, Un[bi], ii, j, k, cfl);
+        }
     }
     if (local) {
         dt = INFINITY;
@@ -1137,6 +1159,7 @@ static double rk_step_impl(const ora_grid *g, double *const *U, const double *co
             const ora_block *b = &g->b[bi];
             long nint = n_interior(b);
             memcpy(Ui[bi], Un[bi], sizeof(double) * NV * b->sv);
+#pragma omp parallel for schedule(static)
             for (int k = 0; k < b->nk; ++k)
                 for (int j = 0; j < b->nj; ++j)
                     for (int ii = 0; ii < b->ni; ++ii) {
@@ -1156,6 +1179,7 @@ static double rk_step_impl(const ora_grid *g, double *const *U, const double *co
     for (int bi = 0; bi < nb; ++bi) {
         const ora_block *b = &g->b[bi];
         long nint = n_interior(b);
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < b->nk; ++k)
             for (int j = 0; j < b->nj; ++j)
                 for (int ii = 0; ii < b->ni; ++ii) {
@@ -1179,6 +1203,21 @@ static double rk_step_impl(const ora_grid *g, double *const *U, const double *co
     free(Un);
     free(Ui);
     return dt;
+}
+
+/* ---- host threads --------------------------------------------------------- */
+
+/* Host threads for the loops over k-planes (n >= 1); returns the count in
+ * effect: 1 when built without OpenMP. */
+int ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* ---- pointwise entry points for the pin tests ---------------------------- */
