@@ -84,7 +84,11 @@ typedef enum {
     SENSEI_BC_INFLOW = 1,       /* fixed freestream state (supersonic inflow / farfield) */
     SENSEI_BC_EXTRAPOLATE = 2,  /* zeroth-order extrapolation (supersonic outflow) */
     SENSEI_BC_SLIP_WALL = 3,    /* mirror: rho, rho e_t copied, momentum m - 2 (m.n) n */
-    SENSEI_BC_INTERFACE = 4     /* copy of a neighbour block's interior layers */
+    SENSEI_BC_INTERFACE = 4,    /* copy of a neighbour block's interior layers */
+    SENSEI_BC_EXTERNAL = 5      /* ghost layers written by the caller (sensei_face_exchange): the
+                                 * face borders cells another worker advances (heterogeneous
+                                 * co-execution, Sec. 4); no kernel of the library writes them.
+                                 * Euler only (SENSEI_ERR_UNSUPPORTED with mu > 0) */
 } sensei_bc_type;
 
 /* Explicit RK schemes, the optimal strong-stability-preserving ones: the
@@ -253,6 +257,16 @@ sensei_status sensei_step_graph_destroy(sensei_step_graph *graph);
 sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk, int *persistent,
                               sensei_stream stream);
 
+/* The schedule stencil launches use (sensei_autotune's choice, or the
+ * default): the k-chunk of a work item, persistent (CTAs = resident CTAs
+ * per SM x SMs, striding over the items) or one CTA per item, work items
+ * in block-major order or by descending cost (longest first, tried by the
+ * autotuner when the blocks differ in size), and the resident CTAs per SM
+ * of the stencil variants measured so far (0 before any launch).  Any
+ * pointer may be NULL. */
+sensei_status sensei_schedule(const sensei_grid *grid, int *kchunk, int *persistent, int *order_by_cost,
+                              int *ctas_per_sm);
+
 /* Instrumentation (not part of the method).  While enabled (enable != 0),
  * every launch of the fused stencil kernel (the residual / Runge-Kutta stage
  * kernel) is bracketed by a CUDA event pair recorded on its own stream, and
@@ -266,6 +280,103 @@ sensei_status sensei_profile_enable(sensei_grid *grid, int enable);
  * NULL).  reset != 0 starts a new interval. */
 sensei_status sensei_profile_read(sensei_grid *grid, double *stencil_ms, long long *stencil_launches,
                                   long long *kernel_launches, int reset);
+
+/* ---- Heterogeneous CPU + GPU co-execution (Sec. 4 workflow, Sec. 6 Eq.
+ * hete, Sec. 7 workload ratio): the cells of one time step split between
+ * the GPU and the host cores, the ghost layers of the cut exchanged every
+ * Runge-Kutta stage.  FP64 Euler only (SENSEI_ERR_UNSUPPORTED otherwise).
+ *
+ * GPU side, stage by stage (the building blocks the co-execution driver
+ * below uses; any caller may use them with SENSEI_BC_EXTERNAL faces): */
+
+/* Stage `stage` (0-based) of one explicit step of RK scheme `rk` with the
+ * time step dt (> 0, host value): stage 0 fills U's ghosts (every face but
+ * the SENSEI_BC_EXTERNAL ones, which must already hold the neighbour's
+ * layers), sets dt and records the norm partials of R(U^n); every stage
+ * writes its output and pushes it into the ghosts it feeds (again not the
+ * external ones); the last stage writes U^{n+1} into U and finalises the
+ * norms (sensei_norms).  The stages of one step must be issued in order on
+ * one stream.  Asynchronous on `stream`. */
+sensei_status sensei_rk_stage(sensei_grid *grid, double *const *U, int rk, int stage, double dt,
+                              sensei_stream stream);
+
+/* The two cell layers next to face `face` of block `block` of the state
+ * that stage `stage` reads (stage 0: the caller's U[block]; stage s > 0:
+ * the internal output of stage s - 1): unpack = 0 copies the two interior
+ * layers (the boundary cell layer first) into buf; unpack = 1 writes buf
+ * into the two ghost layers (the one next to the face first).  buf is
+ * device memory of 5 * 2 * n1 * n2 doubles, layout [v][layer][t2][t1]
+ * with (t1, t2) = (j, k) on i-faces, (i, k) on j-faces, (i, j) on k-faces.
+ * Asynchronous on `stream`. */
+sensei_status sensei_face_exchange(sensei_grid *grid, double *const *U, int block, int stage, int face, double *buf,
+                                   int unpack, sensei_stream stream);
+
+/* The CFL time step of this grid's cells alone: cfl * min |Omega| /
+ * sum_d (|u . Sbar_d| + c |Sbar_d|) over the cells of U (no ghosts read).
+ * Synchronises `stream`; *dt_out is a host double. */
+sensei_status sensei_dt_min(sensei_grid *grid, double *const *U, double cfl, double *dt_out, sensei_stream stream);
+
+/* Host side: one block advanced by host threads (OpenMP) with the same
+ * method in FP64 -- the library's own host implementation, not a fallback:
+ * it runs only as the host share of a co-executed step.  The state is a
+ * host array owned by the worker, layout from sensei_host_layout (2 ghost
+ * layers per side, rows not padded).  Faces take the rules above except
+ * SENSEI_BC_INTERFACE. */
+typedef struct sensei_host_block sensei_host_block;
+
+/* nodes: host (3, nk+1, nj+1, ni+1); scheme->precision must be SENSEI_FP64
+ * and mu 0; threads >= 1. */
+sensei_status sensei_host_create(int ni, int nj, int nk, const double *nodes, const sensei_scheme *scheme, int threads,
+                                 sensei_host_block **out);
+sensei_status sensei_host_destroy(sensei_host_block *h);
+sensei_status sensei_host_set_bc(sensei_host_block *h, int face, int type, const double *prim);
+sensei_status sensei_host_layout(const sensei_host_block *h, sensei_layout *out);
+/* the worker's state U (host, read-write, sensei_host_layout) */
+double *sensei_host_state(sensei_host_block *h);
+/* ghost fill of U (every face but the external ones) */
+sensei_status sensei_host_fill_ghosts(sensei_host_block *h);
+/* R of U (ghosts filled first) into R (host, [5][nk][nj][ni]) */
+sensei_status sensei_host_residual(sensei_host_block *h, double *R);
+/* cfl * min over the worker's cells of |Omega| / sum_d (...) */
+sensei_status sensei_host_dt_min(sensei_host_block *h, double cfl, double *dt_out);
+/* stage `stage` of an explicit step with dt, as sensei_rk_stage */
+sensei_status sensei_host_stage(sensei_host_block *h, int rk, int stage, double dt);
+/* as sensei_face_exchange, on the worker's state; buf is host memory */
+sensei_status sensei_host_face_exchange(sensei_host_block *h, int stage, int face, double *buf, int unpack);
+
+/* The co-execution driver: one 3D block of ni x nj x nk cells, the planes
+ * k < nk - nk_host on the GPU, the last nk_host planes on `threads` host
+ * threads (2 <= nk_host <= nk - 2; the paper's 1D slab split).
+ * bc_type[6] / bc_prim (6 x 5 primitive states, or NULL without inflow
+ * faces) are the block's own rules; the cut faces become
+ * SENSEI_BC_EXTERNAL on both sides, and with periodic k-faces the GPU
+ * part's kmin face borders the host part's kmax face.  Per step: the two
+ * time-step minima are combined on the host; then, per stage, the GPU stage
+ * is launched, the host threads advance their part meanwhile, and the
+ * cut's two layers travel both ways (device -> pinned host -> device)
+ * before the next stage.  workspace: device memory of
+ * sensei_hetero_workspace_size bytes, 256-byte aligned, caller-owned (the
+ * GPU part's grid workspace, its state and the exchange buffers).  The
+ * driver allocates pinned host buffers of its own. */
+typedef struct sensei_hetero sensei_hetero;
+
+sensei_status sensei_hetero_workspace_size(const sensei_block_desc *block, const sensei_scheme *scheme, int nk_host,
+                                           size_t *bytes);
+/* nodes: host (3, nk+1, nj+1, ni+1) of the whole block */
+sensei_status sensei_hetero_create(const sensei_block_desc *block, const double *nodes, const sensei_scheme *scheme,
+                                   const int *bc_type, const double *bc_prim, int nk_host, int threads,
+                                   void *workspace, size_t workspace_bytes, sensei_stream stream,
+                                   sensei_hetero **out);
+sensei_status sensei_hetero_destroy(sensei_hetero *h);
+/* the whole block's interior state, host (5, nk, nj, ni): in and out */
+sensei_status sensei_hetero_upload(sensei_hetero *h, const double *U);
+sensei_status sensei_hetero_download(sensei_hetero *h, double *U);
+/* One step; cfl > 0: dt = cfl * min over both parts, else dt > 0 as given.
+ * *dt_used (host, may be NULL) receives dt; times_ms (host, 4 doubles, may
+ * be NULL) receives the step's wall time, the GPU stages' time (events),
+ * the host stages' time and the exchange time (the part of the wall time
+ * spent neither in a host stage nor waiting for the GPU). */
+sensei_status sensei_hetero_step(sensei_hetero *h, int rk, double cfl, double dt, double *dt_used, double *times_ms);
 
 /* Residual norms that allocate nothing.  The paper has no counterpart: this
  * exists for callers that cannot allocate device memory, e.g. a solver

@@ -1,8 +1,10 @@
 """Build the CUDA library ``libsensei.so`` in-tree (``paper_2305_18057_gb300/_build``).
 
 nvcc compiles every ``csrc/*.cu`` for sm_103a only (``-gencode
-arch=compute_103a,code=sm_103a``), the translation units in parallel, then
-links a shared library exporting the C ABI of ``include/sensei.h``.
+arch=compute_103a,code=sm_103a``), the host compiler every ``csrc/*.cpp``
+(the host worker of co-execution, OpenMP), the translation units in
+parallel, then nvcc links a shared library exporting the C ABI of
+``include/sensei.h``.
 """
 from __future__ import annotations
 
@@ -35,10 +37,17 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _host_sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cpp")))
+
+
+HOST_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-fopenmp", "-I", INCLUDE]
+
+
 def _fingerprint() -> str:
     h = hashlib.sha256()
-    for p in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "sensei.h"),
-                                                                           __file__]:
+    for p in _sources() + _host_sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
+            os.path.join(INCLUDE, "sensei.h"), __file__]:
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())
             h.update(f.read())
@@ -62,6 +71,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         if verbose:
             cmd += ["-Xptxas", "-v"]
         cmds.append(cmd)
+    # the host worker of heterogeneous co-execution: C++ with OpenMP
+    for src in _host_sources():
+        obj = os.path.join(BUILD, os.path.basename(src)[:-4] + ".host.o")
+        objs.append(obj)
+        cmds.append([os.environ.get("CXX", "g++"), *HOST_FLAGS, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -74,7 +88,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             if verbose and (r.stdout or r.stderr):
                 sys.stderr.write(r.stdout + r.stderr)
     tmp = LIB + f".{os.getpid()}.tmp"
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    r = subprocess.run([cc, *ARCH, "-shared", "-Xcompiler", "-fopenmp", "-o", tmp, *objs, "-lgomp"],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

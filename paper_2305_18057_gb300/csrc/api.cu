@@ -69,8 +69,8 @@ struct HostBlock {
 struct Plan {
     std::vector<HostBlock> blocks;
     std::vector<size_t> off_fn, off_fdf, off_rec32, off_vol, off_ivol, off_sbar, off_sbar32, off_dtv, off_stage, off_wv,
-        off_rvis, off_fvis, off_gvis;
-    size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0;
+        off_rvis, off_fvis, off_gvis, off_tmap;
+    size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0, off_order = 0;
     size_t bytes = 0;
     long long max_items = 0;   // partial slots (items at the smallest k-chunk)
     long long ncells = 0;
@@ -150,7 +150,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     P.blocks.resize(nblocks);
     for (auto *v : {&P.off_fn, &P.off_fdf, &P.off_rec32, &P.off_vol, &P.off_ivol, &P.off_sbar, &P.off_sbar32, &P.off_dtv,
                     &P.off_wv, &P.off_rvis, &P.off_fvis, &P.off_gvis,
-                    &P.off_stage})
+                    &P.off_stage, &P.off_tmap})
         v->resize(nblocks);
     const bool f32 = scheme->precision == SENSEI_FP32_FLUX || scheme->precision == SENSEI_FP32_STORE;
     P.two_d = blocks[0].nk == 1;
@@ -214,6 +214,8 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
         P.off_gvis[b] = vis ? take(cur, 3 * GVIS * mv * sizeof(double)) : 0;
         // two FP64 stage states, or two FP32 stage states + two FP32 increments
         P.off_stage[b] = take(cur, 2 * (size_t)B.L.elems * sizeof(double));
+        // the tensor maps of the state slots (3D FP32 arithmetic)
+        P.off_tmap[b] = f32 && !H.two_d ? take(cur, 5 * (size_t)TMAP_BYTES) : 0;
     }
     // partial slots for the finest schedule
     P.max_items = assign_items(P.blocks, KCHUNK_MIN);
@@ -227,6 +229,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     assign_items(P.blocks, kchunk);
     P.off_desc = take(cur, (size_t)nblocks * sizeof(BlockDev));
     P.off_partials = take(cur, (size_t)P.max_items * 3 * NV * sizeof(double));
+    P.off_order = take(cur, (size_t)P.max_items * sizeof(int));
     P.off_dtbits = take(cur, sizeof(unsigned long long));
     P.off_dtslot = take(cur, sizeof(double));
     P.off_norms = take(cur, 16 * sizeof(double));   // 15 norms + the error word
@@ -276,7 +279,13 @@ struct sensei_grid {
     long long wait_limit = 1LL << 31;   // bounded device waits (sensei_debug_set)
     unsigned tx_extra = 0;
     bool stage_ghosts = false;  // fixed (inflow) ghosts of the stage buffers set
+    // tensor maps of the state slots (3D FP32 grids): host copies, and the
+    // caller's state pointer each block's SLOT_USER map was encoded for
+    std::vector<unsigned char> tmaps_host;
+    std::vector<const void *> tmap_user;
     int grid_mode = 0;          // 0: persistent (resident CTAs x SMs), 1: one CTA per item
+    int order_mode = 0;         // 0: items block-major; 1: by descending cost (longest first)
+    int *order = nullptr;       // device: launch position -> item (order_mode 1)
     int ctas_cache[4] = {0, 0, 0, 0};
     // instrumentation
     bool prof = false;
@@ -339,14 +348,44 @@ int stencil_grid(sensei_grid *g, int kind, long long nitems)
     return (int)std::min<long long>(nitems, (long long)g->ctas_cache[kind] * g->sms);
 }
 
-// Upload the descriptor table if boundary rules or the schedule changed.
-// Synchronises `s` (a pageable host-to-device copy); never inside a capture.
+// The work items of the current assignment by descending cost, longest
+// first (so that a launch's last wave holds the short ones): an item's cost
+// is its k-planes plus the two warm-up planes of the FP32 stencil (a tile
+// costs about the same whether its columns are all inside the block or
+// not); ties keep block-major order.
+std::vector<int> items_by_cost(const std::vector<HostBlock> &blocks)
+{
+    std::vector<std::pair<int, int>> cost;   // (-cost, item)
+    for (const HostBlock &H : blocks) {
+        const BlockDev &B = H.dev;
+        const long long per_chunk = (long long)B.tiles_i * B.tiles_j;
+        for (int ch = 0; ch < B.nchunks; ++ch) {
+            const int planes = H.two_d ? 1 : std::min(B.kchunk, B.nk - ch * B.kchunk);
+            for (long long t = 0; t < per_chunk; ++t)
+                cost.push_back({-(planes + 2), (int)(B.item0 + ch * per_chunk + t)});
+        }
+    }
+    std::stable_sort(cost.begin(), cost.end(),
+                     [](const std::pair<int, int> &a, const std::pair<int, int> &b) { return a.first < b.first; });
+    std::vector<int> order(cost.size());
+    for (size_t n = 0; n < cost.size(); ++n) order[n] = cost[n].second;
+    return order;
+}
+
+// Upload the descriptor table (and the item order) if boundary rules or the
+// schedule changed.  Synchronises `s` (a pageable host-to-device copy);
+// never inside a capture.
 sensei_status sync_descriptors(sensei_grid *g, cudaStream_t s)
 {
     if (!g->dirty) return SENSEI_OK;
     std::vector<BlockDev> tab(g->plan.blocks.size());
     for (size_t b = 0; b < tab.size(); ++b) tab[b] = g->plan.blocks[b].dev;
     CUDA_TRY(cudaMemcpyAsync(g->desc, tab.data(), tab.size() * sizeof(BlockDev), cudaMemcpyHostToDevice, s));
+    std::vector<int> order;
+    if (g->order_mode == 1) {
+        order = items_by_cost(g->plan.blocks);
+        CUDA_TRY(cudaMemcpyAsync(g->order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
     if (g->scheme.mu > 0.0) {
         // the viscous face metrics follow the boundary rules (the geometry a
         // ghost cell carries)
@@ -483,6 +522,7 @@ void fill_params(BatchParams<R> &p, const sensei_grid *g, const StencilCall &c)
     p.dt_slot = c.dt_slot;
     p.dt_scale = c.dt_scale;
     p.partials = c.partials ? g->partials : nullptr;
+    p.order = g->order_mode == 1 ? g->order : nullptr;
     p.err = g->err;
     for (int b = 0; b < nb; ++b) {
         p.user[b] = c.user ? c.user[b] : nullptr;
@@ -491,8 +531,14 @@ void fill_params(BatchParams<R> &p, const sensei_grid *g, const StencilCall &c)
     }
 }
 
+sensei_status ensure_user_maps(sensei_grid *g, double *const *U, cudaStream_t s);
+
 sensei_status stencil_launch(sensei_grid *g, const StencilCall &c, cudaStream_t s)
 {
+    if (c.in_slot == SLOT_USER) {
+        sensei_status st = ensure_user_maps(g, c.user, s);
+        if (st != SENSEI_OK) return st;
+    }
     const bool in_f32 = c.in_slot == SLOT_X0 || c.in_slot == SLOT_X1;
     const int kind = precision_kind(g, in_f32);
     const long long nitems = total_items(g->plan.blocks);
@@ -550,12 +596,38 @@ const int RK_STAGES[3] = {2, 3, 4};
 
 bool incr_mode(const sensei_grid *g) { return g->scheme.precision == SENSEI_FP32_STORE; }
 
+// The SLOT_USER tensor maps of the FP32 stencil for the caller's state
+// pointers: re-encoded and uploaded (stream-ordered) when a pointer differs
+// from the one a map was made for.  Not inside a stream capture: the
+// capturing entry points run prepare_step, which calls this, first.
+sensei_status ensure_user_maps(sensei_grid *g, double *const *U, cudaStream_t s)
+{
+    if (!U || g->tmap_user.empty()) return SENSEI_OK;
+    for (size_t b = 0; b < g->plan.blocks.size(); ++b) {
+        const BlockDev &B = g->plan.blocks[b].dev;
+        if (!B.tmaps || g->tmap_user[b] == U[b]) continue;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(SENSEI_ERR_STATE, "state pointers changed inside a stream capture");
+        unsigned char *h = g->tmaps_host.data() + b * 5 * TMAP_BYTES;
+        if (!encode_state_map(h, U[b], B, false))
+            return fail(SENSEI_ERR_CUDA, "cuTensorMapEncodeTiled rejected the state of block %zu", b);
+        CUDA_TRY(cudaMemcpyAsync((void *)B.tmaps, h, TMAP_BYTES, cudaMemcpyHostToDevice, s));
+        g->tmap_user[b] = U[b];
+    }
+    return SENSEI_OK;
+}
+
 // Everything of a step that must not happen inside a stream capture: the
-// descriptor upload and the one-time ghost fill of the stage buffers (it
-// sets their fixed inflow ghosts; all other ghosts are pushed every stage).
-sensei_status prepare_step(sensei_grid *g, cudaStream_t s)
+// descriptor upload, the tensor maps of the caller's states and the
+// one-time ghost fill of the stage buffers (it sets their fixed inflow
+// ghosts; all other ghosts are pushed every stage).
+sensei_status prepare_step(sensei_grid *g, double *const *U, cudaStream_t s)
 {
     sensei_status st = sync_descriptors(g, s);
+    if (st != SENSEI_OK) return st;
+    st = ensure_user_maps(g, U, s);
     if (st != SENSEI_OK) return st;
     if (!g->stage_ghosts) {
         const bool incr = incr_mode(g);
@@ -763,6 +835,7 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
     g->dt_bits = (unsigned long long *)(g->ws + P.off_dtbits);
     g->dt_slot = (double *)(g->ws + P.off_dtslot);
     g->norms = (double *)(g->ws + P.off_norms);
+    g->order = (int *)(g->ws + P.off_order);
     g->err = (unsigned *)(g->norms + 15);
     for (int b = 0; b < nblocks; ++b) {
         BlockDev &B = g->plan.blocks[b].dev;
@@ -787,6 +860,7 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
         B.xs[1] = B.xs[0] + B.L.elems;
         B.ds[0] = B.xs[1] + B.L.elems;
         B.ds[1] = B.ds[0] + B.L.elems;
+        B.tmaps = P.off_tmap[b] ? (const unsigned char *)(g->ws + P.off_tmap[b]) : nullptr;
         MetricsOut mo;
         memset(&mo, 0, sizeof mo);
         for (int fam = 0; fam < 3; ++fam)
@@ -810,6 +884,26 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
     if (e != cudaSuccess) {
         delete g;
         return fail(SENSEI_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    // tensor maps of the internal state slots (fixed addresses); the
+    // SLOT_USER maps follow the caller's pointers (ensure_user_maps)
+    g->tmaps_host.assign((size_t)nblocks * 5 * TMAP_BYTES, 0);
+    g->tmap_user.assign(nblocks, nullptr);
+    for (int b = 0; b < nblocks; ++b) {
+        const BlockDev &B = g->plan.blocks[b].dev;
+        if (!B.tmaps) continue;
+        unsigned char *h = g->tmaps_host.data() + (size_t)b * 5 * TMAP_BYTES;
+        const void *bases[5] = {nullptr, B.st64[0], B.st64[1], B.xs[0], B.xs[1]};
+        for (int slot = SLOT_ST0; slot <= SLOT_X1; ++slot)
+            if (!encode_state_map(h + slot * TMAP_BYTES, bases[slot], B, slot >= SLOT_X0)) {
+                delete g;
+                return fail(SENSEI_ERR_CUDA, "cuTensorMapEncodeTiled rejected the state slot %d of block %d", slot, b);
+            }
+        e = cudaMemcpyAsync((void *)B.tmaps, h, 5 * TMAP_BYTES, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            delete g;
+            return fail(SENSEI_ERR_CUDA, "uploading tensor maps: %s", cudaGetErrorString(e));
+        }
     }
     *out = g;
     g_msg[0] = 0;
@@ -854,8 +948,10 @@ sensei_status sensei_set_bc(sensei_grid *grid, int block, int face, int type, co
     BlockDev &B = H.dev;
     if (face < 0 || face >= (H.two_d ? 4 : 6))
         return fail(SENSEI_ERR_INVALID_ARG, "face %d out of range for a %s block", face, H.two_d ? "2D" : "3D");
-    if (type < SENSEI_BC_PERIODIC || type > SENSEI_BC_INTERFACE)
+    if (type < SENSEI_BC_PERIODIC || type > SENSEI_BC_EXTERNAL)
         return fail(SENSEI_ERR_INVALID_ARG, "unknown boundary type %d", type);
+    if (type == SENSEI_BC_EXTERNAL && grid->scheme.mu > 0.0)
+        return fail(SENSEI_ERR_UNSUPPORTED, "caller-written ghost layers with the viscous flux");
     const int axis = face >> 1;
     const int n_own = axis == 0 ? B.ni : axis == 1 ? B.nj : B.nk;
     // every rule reads or feeds the two cell layers next to a boundary
@@ -957,10 +1053,109 @@ sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double
     Device dev;
     CUDA_TRY(dev.set(grid->device));
     cudaStream_t s = (cudaStream_t)stream;
-    st = prepare_step(grid, s);
+    st = prepare_step(grid, U, s);
     if (st == SENSEI_OK) st = rk_step_launches(grid, U, rk, cfl, dt, dt_used, s);
     if (st == SENSEI_OK) g_msg[0] = 0;
     return st;
+}
+
+sensei_status sensei_rk_stage(sensei_grid *grid, double *const *U, int rk, int stage, double dt,
+                              sensei_stream stream)
+{
+    TraceRange trace("sensei_rk_stage");
+    sensei_status st = check_step_args(grid, U, rk, 0.0, dt);
+    if (st != SENSEI_OK) return st;
+    if (grid->scheme.precision != SENSEI_FP64 || viscous(grid))
+        return fail(SENSEI_ERR_UNSUPPORTED, "stage-by-stage stepping runs the FP64 Euler form");
+    const int S = RK_STAGES[rk];
+    if (stage < 0 || stage >= S) return fail(SENSEI_ERR_INVALID_ARG, "stage %d out of range (%d stages)", stage, S);
+    Device dev;
+    CUDA_TRY(dev.set(grid->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (stage == 0) {
+        st = prepare_step(grid, U, s);
+        if (st == SENSEI_OK) st = fill_slot(grid, SLOT_USER, U, s);
+        if (st != SENSEI_OK) return st;
+        CUDA_TRY(launch_set_scalar(grid->dt_slot, dt, s));
+        grid->kernel_launches++;
+    }
+    const double *co = RK_COEF[rk][stage];
+    StencilCall c;
+    memset(&c, 0, sizeof c);
+    c.alpha = co[0];
+    c.beta = co[1];
+    c.gdt = co[2];
+    c.dt_slot = grid->dt_slot;
+    c.dt_scale = 1.0;
+    c.partials = stage == 0;
+    c.user = U;
+    c.push = 1;
+    c.dprev = -1;
+    c.dout = -1;
+    c.mode = MODE_ACCUM;
+    c.in_slot = stage == 0 ? SLOT_USER : SLOT_ST0 + (stage - 1) % 2;
+    c.out_slot = stage == S - 1 ? SLOT_USER : SLOT_ST0 + stage % 2;
+    st = stencil(grid, c, s);
+    if (st != SENSEI_OK) return st;
+    if (stage == S - 1) {
+        CUDA_TRY(launch_norms_finalize(grid->partials, (int)total_items(grid->plan.blocks), grid->plan.ncells,
+                                       grid->norms, s));
+        grid->kernel_launches++;
+    }
+    g_msg[0] = 0;
+    return SENSEI_OK;
+}
+
+sensei_status sensei_face_exchange(sensei_grid *grid, double *const *U, int block, int stage, int face, double *buf,
+                                   int unpack, sensei_stream stream)
+{
+    sensei_status st = check_grid(grid);
+    if (st == SENSEI_OK) st = check_states(grid, U, "U");
+    if (st != SENSEI_OK) return st;
+    if (block < 0 || block >= (int)grid->plan.blocks.size())
+        return fail(SENSEI_ERR_INVALID_ARG, "block %d out of range", block);
+    const HostBlock &H = grid->plan.blocks[block];
+    if (face < 0 || face >= (H.two_d ? 4 : 6)) return fail(SENSEI_ERR_INVALID_ARG, "face %d out of range", face);
+    if (stage < 0 || stage > 3) return fail(SENSEI_ERR_INVALID_ARG, "stage %d out of range", stage);
+    if (!buf) return fail(SENSEI_ERR_INVALID_ARG, "buf is NULL");
+    if (grid->scheme.precision != SENSEI_FP64)
+        return fail(SENSEI_ERR_UNSUPPORTED, "face exchange of the FP64 stage states only");
+    Device dev;
+    CUDA_TRY(dev.set(grid->device));
+    const BlockDev &B = H.dev;
+    double *u = stage == 0 ? U[block] : B.st64[(stage - 1) % 2];
+    CUDA_TRY(launch_face_exchange(B, u, face, buf, unpack ? 1 : 0, (cudaStream_t)stream));
+    grid->kernel_launches++;
+    g_msg[0] = 0;
+    return SENSEI_OK;
+}
+
+sensei_status sensei_dt_min(sensei_grid *grid, double *const *U, double cfl, double *dt_out, sensei_stream stream)
+{
+    sensei_status st = check_grid(grid);
+    if (st == SENSEI_OK) st = check_states(grid, U, "U");
+    if (st != SENSEI_OK) return st;
+    if (!dt_out || !(cfl > 0.0)) return fail(SENSEI_ERR_INVALID_ARG, "need cfl > 0 and an output");
+    Device dev;
+    CUDA_TRY(dev.set(grid->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    st = sync_descriptors(grid, s);
+    if (st != SENSEI_OK) return st;
+    const long long nitems = total_items(grid->plan.blocks);
+    int kchunk = 1;
+    for (const HostBlock &H : grid->plan.blocks) kchunk = std::max(kchunk, H.dev.kchunk);
+    CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
+    CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, 0, cfl,
+                       grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms), kchunk,
+                       grid->scheme.precision == SENSEI_FP32_FLUX || grid->scheme.precision == SENSEI_FP32_STORE,
+                       viscous_dt_factor(grid), s));
+    grid->kernel_launches++;
+    double m = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&m, grid->dt_bits, sizeof m, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *dt_out = cfl * m;
+    g_msg[0] = 0;
+    return SENSEI_OK;
 }
 
 sensei_status sensei_rk_step_local(sensei_grid *grid, double *const *U, int rk, double cfl, double *dt_min,
@@ -973,7 +1168,7 @@ sensei_status sensei_rk_step_local(sensei_grid *grid, double *const *U, int rk, 
     Device dev;
     CUDA_TRY(dev.set(grid->device));
     cudaStream_t s = (cudaStream_t)stream;
-    st = prepare_step(grid, s);
+    st = prepare_step(grid, U, s);
     if (st == SENSEI_OK) st = rk_step_launches(grid, U, rk, cfl, 0.0, dt_min, s, true);
     if (st == SENSEI_OK) g_msg[0] = 0;
     return st;
@@ -989,7 +1184,7 @@ sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int 
     Device dev;
     CUDA_TRY(dev.set(grid->device));
     cudaStream_t s = (cudaStream_t)stream;
-    st = prepare_step(grid, s);
+    st = prepare_step(grid, U, s);
     if (st != SENSEI_OK) return st;
     CUDA_TRY(cudaStreamSynchronize(s));
     // capture on a private stream: the caller's may be the legacy stream
@@ -1055,7 +1250,7 @@ sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk_o
     Device dev;
     CUDA_TRY(dev.set(grid->device));
     cudaStream_t s = (cudaStream_t)stream;
-    st = prepare_step(grid, s);
+    st = prepare_step(grid, U, s);
     if (st == SENSEI_OK) st = fill_slot(grid, SLOT_USER, U, s);
     if (st != SENSEI_OK) return st;
     // first-stage launches with dt = 0 into the stage buffers: they time the
@@ -1082,11 +1277,16 @@ sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk_o
     const bool prof = grid->prof;
     grid->prof = false;
     float best = 1e30f;
-    int best_k = grid->plan.blocks[0].dev.kchunk, best_mode = grid->grid_mode;
+    int best_k = grid->plan.blocks[0].dev.kchunk, best_mode = grid->grid_mode, best_order = grid->order_mode;
+    // item orders: block-major, and by cost when the blocks differ in size
+    // (one block: every item but a last shorter chunk costs the same)
+    const int orders = grid->plan.blocks.size() > 1 ? 2 : 1;
     for (int kc : KCHUNK_CANDIDATES) {
         if (grid->plan.two_d && kc != KCHUNK_CANDIDATES[0]) continue;
         if (kc > 2 * max_nk) continue;
         assign_items(grid->plan.blocks, kc);
+        for (int om = 0; om < orders && st == SENSEI_OK; ++om) {
+        grid->order_mode = om;
         grid->dirty = true;
         st = sync_descriptors(grid, s);
         if (st != SENSEI_OK) break;
@@ -1107,7 +1307,9 @@ sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk_o
                 best = ms;
                 best_k = kc;
                 best_mode = mode;
+                best_order = om;
             }
+        }
         }
         if (st != SENSEI_OK) break;
     }
@@ -1116,12 +1318,32 @@ sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk_o
     cudaEventDestroy(e1);
     assign_items(grid->plan.blocks, best_k);
     grid->grid_mode = best_mode;
+    grid->order_mode = best_order;
     grid->dirty = true;
     sensei_status st2 = sync_descriptors(grid, s);
     if (st == SENSEI_OK) st = st2;
     if (st != SENSEI_OK) return st;
     if (kchunk_out) *kchunk_out = best_k;
     if (persistent_out) *persistent_out = best_mode == 0;
+    g_msg[0] = 0;
+    return SENSEI_OK;
+}
+
+sensei_status sensei_schedule(const sensei_grid *grid, int *kchunk, int *persistent, int *order_by_cost,
+                              int *ctas_per_sm)
+{
+    sensei_status st = check_grid(grid);
+    if (st != SENSEI_OK) return st;
+    int kc = 1;
+    for (const HostBlock &H : grid->plan.blocks) kc = std::max(kc, H.dev.kchunk);
+    if (kchunk) *kchunk = kc;
+    if (persistent) *persistent = grid->grid_mode == 0;
+    if (order_by_cost) *order_by_cost = grid->order_mode == 1;
+    if (ctas_per_sm) {
+        int best = 0;
+        for (int kind = 0; kind < 4; ++kind) best = std::max(best, grid->ctas_cache[kind]);
+        *ctas_per_sm = best;
+    }
     g_msg[0] = 0;
     return SENSEI_OK;
 }

@@ -192,6 +192,7 @@ __device__ __forceinline__ void fill_one(const BCBatch &p, const BlockDev &B, in
 {
     T *U = slot_buffer<T>(B, p.user[b], p.slot);
     const int type = B.bc_type[f];
+    if (type == SENSEI_BC_EXTERNAL) return;   // written by the caller
     int gi, gj, gk, mi, mj, mk, a, bb, c;
     face_cells(f, B.ni, B.nj, B.nk, t1, t2, layer, 0, gi, gj, gk, a, bb, c);
     T q[NV];
@@ -233,6 +234,31 @@ __device__ __forceinline__ void fill_one(const BCBatch &p, const BlockDev &B, in
     }
     const long long gc = cell_index(B.L, gi, gj, gk);
     for (int v = 0; v < NV; ++v) U[gc + v * B.L.sv] = q[v];
+}
+
+// The two cell layers next to face f of one state array (heterogeneous
+// co-execution): pack copies the interior layers l = 0, 1 inside the face
+// into buf[v][l][t2][t1]; unpack writes buf into the ghost layers l + 1
+// outside it (a neighbour's interior layer l is this block's ghost layer
+// l + 1).
+__global__ void face_exchange_kernel(BlockDev B, double *u, int f, double *buf, int unpack)
+{
+    const int n1 = f < 2 ? B.nj : B.ni, n2 = f < 4 ? B.nk : B.nj;
+    const long long face = (long long)n1 * n2, per = NG * face, total = NV * per;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(t / per);
+        const long long r = t - v * per;
+        const int l = (int)(r / face);
+        const long long q = r - l * face;
+        const int t2 = (int)(q / n1), t1 = (int)(q - (long long)t2 * n1);
+        int gi, gj, gk, mi, mj, mk;
+        face_cells(f, B.ni, B.nj, B.nk, t1, t2, l + 1, l, gi, gj, gk, mi, mj, mk);
+        if (unpack)
+            u[cell_index(B.L, gi, gj, gk) + v * B.L.sv] = buf[t];
+        else
+            buf[t] = u[cell_index(B.L, mi, mj, mk) + v * B.L.sv];
+    }
 }
 
 template <typename T>
@@ -352,6 +378,15 @@ cudaError_t launch_edges(const BCBatch &p, int max_units, cudaStream_t s)
         edge_kernel<float><<<grid, 256, 0, s>>>(p);
     else
         edge_kernel<double><<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_exchange(const BlockDev &B, double *u, int f, double *buf, int unpack, cudaStream_t s)
+{
+    const long long n1 = f < 2 ? B.nj : B.ni, n2 = f < 4 ? B.nk : B.nj;
+    const long long total = NV * NG * n1 * n2;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    face_exchange_kernel<<<blocks, 256, 0, s>>>(B, u, f, buf, unpack);
     return cudaGetLastError();
 }
 

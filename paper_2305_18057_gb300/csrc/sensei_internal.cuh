@@ -95,6 +95,11 @@ struct BlockDev {
     double *gvis;           // viscous: face-gradient metrics, [family * GVIS + n][mvolume] (viscous.cu)
     double *st64[2];        // FP64 stage states
     float *xs[2], *ds[2];   // FP32 stage states and increments
+    // 3D FP32-arithmetic grids: one 128-byte tensor map per state slot
+    // (SLOT_USER .. SLOT_X1) describing the slot's ghosted array as a 4D
+    // tensor (padded row, rows, planes, variables) for the bulk tensor copy
+    // of a stencil tile; null otherwise
+    const unsigned char *tmaps;
     int tiles_i, tiles_j, kchunk, nchunks;
     long long item0;        // first work item
     long long bc0;          // first ghost-fill work unit
@@ -142,6 +147,7 @@ struct BatchParams {
     const double *dt_slot;  // dt = dt_scale * *dt_slot
     double dt_scale;
     double *partials;       // 15 doubles per item (null: no norms)
+    const int *order;       // launch position -> work item (null: block-major); item costs descending
     unsigned *err;
     double *user[MAX_BLOCKS];        // the caller's U, per block
     double *rout[MAX_BLOCKS];        // MODE_RESIDUAL: R[5][nk][nj][ni]
@@ -174,6 +180,8 @@ struct BCBatch {
 cudaError_t launch_metrics(int ni, int nj, int nk, const double *X, const MetricsOut &mo,
                            const MetricLayout &ml, cudaStream_t s);
 cudaError_t launch_bc(const BCBatch &p, cudaStream_t s);
+// the two cell layers next to face f of state u: pack (interior) or unpack (ghosts)
+cudaError_t launch_face_exchange(const BlockDev &B, double *u, int f, double *buf, int unpack, cudaStream_t s);
 // the block-edge ghosts of every block of one slot (after launch_bc of the
 // slot); max_units: the largest per-block count, 16 (ni + nj + nk)
 cudaError_t launch_edges(const BCBatch &p, int max_units, cudaStream_t s);
@@ -186,6 +194,9 @@ cudaError_t launch_stencil_f64(const BatchParams<double> &p, int limiter, bool t
 cudaError_t launch_stencil_f32(const BatchParams<float> &p, int limiter, bool two_d, int grid, cudaStream_t s);
 // FP32 arithmetic on an FP32 stage state
 cudaError_t launch_stencil_f32s(const BatchParams<float> &p, int limiter, bool two_d, int grid, cudaStream_t s);
+// the 3D FP32-arithmetic kernel with paired face fluxes (in_f32: on an FP32 stage state)
+cudaError_t launch_stencil32p(const BatchParams<float> &p, int limiter, bool in_f32, int grid, cudaStream_t s);
+int stencil32p_ctas_per_sm(int limiter, bool in_f32);
 // double-float arithmetic on an FP64 state
 cudaError_t launch_stencil_df64(const BatchParams<df64> &p, int limiter, bool two_d, int grid, cudaStream_t s);
 int stencil_ctas_per_sm_df64(int limiter, bool two_d);
@@ -213,6 +224,12 @@ cudaError_t launch_set_scalar(double *slot, double v, cudaStream_t s);
 cudaError_t launch_scale_copy(double *dst, const double *src, double scale, cudaStream_t s);
 // Record the thread-local message returned by sensei_last_error (api.cu).
 sensei_status fail_status(sensei_status st, const char *fmt, ...);
+
+// Encode the tensor map of one state slot of block B (base: the slot's
+// array; f32: FP32 elements, else FP64) into out (128 bytes); false if the
+// driver rejects it
+bool encode_state_map(void *out, const void *base, const BlockDev &B, bool f32);
+constexpr int TMAP_BYTES = 128;
 
 cudaError_t launch_norms_finalize(const double *partials, int nparts, long long ncells, double *out15,
                                   cudaStream_t s);

@@ -499,7 +499,8 @@ __device__ __forceinline__ float *out_buffer<float>(const BlockDev &N, double *,
 // ghost cell it feeds (the ghost rules of the boundary fill, applied from
 // the producing side): interface and periodic ghosts of layer m+1 for the
 // cell m cells inside a face, the mirrored wall ghost of layer m+1, both
-// extrapolation ghosts from the boundary cell.  Inflow ghosts are fixed.
+// extrapolation ghosts from the boundary cell.  Inflow ghosts are fixed;
+// caller-written (external) ghosts are the caller's.
 template <typename T, typename R>
 __device__ __noinline__ void push_ghosts(const BatchParams<R> &p, const BlockDev &B, int b, int i, int j, int k,
                                          const T q[NV], int nfaces)
@@ -516,7 +517,8 @@ __device__ __noinline__ void push_ghosts(const BatchParams<R> &p, const BlockDev
         }
         if (m > 1) continue;
         const int type = B.bc_type[f];
-        if (type == SENSEI_BC_INFLOW || (type == SENSEI_BC_EXTRAPOLATE && m != 0)) continue;
+        if (type == SENSEI_BC_INFLOW || type == SENSEI_BC_EXTERNAL || (type == SENSEI_BC_EXTRAPOLATE && m != 0))
+            continue;
         int t1, t2;
         tangential(f, i, j, k, t1, t2);
         int gi, gj, gk, a, c, d;
@@ -592,7 +594,8 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
 
     // persistent: CTA x takes items x, x + grid, x + 2 grid, ...
-    for (long long item = blockIdx.x; item < p.nitems; item += gridDim.x) {
+    for (long long pos = blockIdx.x; pos < p.nitems; pos += gridDim.x) {
+        const long long item = p.order ? p.order[pos] : pos;
         const int b = find_block_item(p.blocks, p.nblocks, item);
         __syncthreads();   // the previous item is done with sB and the shared tiles
         {

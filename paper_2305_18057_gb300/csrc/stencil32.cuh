@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
     uint32_t phase = 0;     // bit n: parity of buffer n's next phase
     bool failed = false;
 
-    for (long long item = blockIdx.x; item < p.nitems && !failed; item += gridDim.x) {
+    for (long long pos = blockIdx.x; pos < p.nitems && !failed; pos += gridDim.x) {
+        const long long item = p.order ? p.order[pos] : pos;
         const int b = find_block_item(p.blocks, p.nblocks, item);
         __syncthreads();   // the previous item is done with sB and every tile buffer
         {

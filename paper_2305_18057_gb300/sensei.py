@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libsensei.so")
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NONPHYSICAL, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_STATE = range(7)
 FP64, FP32_FLUX, FP32_STORE, DF64 = 0, 1, 2, 3
-BC_PERIODIC, BC_INFLOW, BC_EXTRAPOLATE, BC_SLIP_WALL, BC_INTERFACE = range(5)
+BC_PERIODIC, BC_INFLOW, BC_EXTRAPOLATE, BC_SLIP_WALL, BC_INTERFACE, BC_EXTERNAL = range(6)
 RK2_SSP, RK3_SSP, RK4_SSP2 = range(3)
 LIM_NONE, LIM_MINMOD, LIM_VANLEER = range(3)
 NV = 5
@@ -31,6 +31,12 @@ EXPORTS = ("sensei_workspace_size", "sensei_create_grid", "sensei_destroy_grid",
            "sensei_set_bc", "sensei_fill_ghosts", "sensei_residual", "sensei_rk_step", "sensei_norms",
            "sensei_rk_step_local", "sensei_step_graph_create", "sensei_step_graph_launch", "sensei_step_graph_destroy", "sensei_autotune",
            "sensei_profile_enable", "sensei_profile_read", "sensei_residual_norms_noalloc", "sensei_debug_set",
+           "sensei_rk_stage", "sensei_face_exchange", "sensei_dt_min", "sensei_schedule",
+           "sensei_host_create", "sensei_host_destroy", "sensei_host_set_bc", "sensei_host_layout",
+           "sensei_host_state", "sensei_host_fill_ghosts", "sensei_host_residual", "sensei_host_dt_min",
+           "sensei_host_stage", "sensei_host_face_exchange",
+           "sensei_hetero_workspace_size", "sensei_hetero_create", "sensei_hetero_destroy", "sensei_hetero_upload",
+           "sensei_hetero_download", "sensei_hetero_step",
            "sensei_last_error")
 
 
@@ -89,10 +95,33 @@ def load(path: str = LIB_PATH):
     L.sensei_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
     L.sensei_residual_norms_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, dp, vp]
     L.sensei_debug_set.argtypes = [vp, C.c_int, C.c_longlong]
+    L.sensei_rk_stage.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_int, C.c_double, vp]
+    ip = C.POINTER(C.c_int)
+    L.sensei_schedule.argtypes = [vp, ip, ip, ip, ip]
+    L.sensei_face_exchange.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_int, C.c_int, vp, C.c_int, vp]
+    L.sensei_dt_min.argtypes = [vp, C.POINTER(vp), C.c_double, dp, vp]
+    L.sensei_host_create.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.POINTER(Scheme), C.c_int, C.POINTER(vp)]
+    L.sensei_host_destroy.argtypes = [vp]
+    L.sensei_host_set_bc.argtypes = [vp, C.c_int, C.c_int, dp]
+    L.sensei_host_layout.argtypes = [vp, C.POINTER(Layout)]
+    L.sensei_host_state.argtypes = [vp]
+    L.sensei_host_fill_ghosts.argtypes = [vp]
+    L.sensei_host_residual.argtypes = [vp, dp]
+    L.sensei_host_dt_min.argtypes = [vp, C.c_double, dp]
+    L.sensei_host_stage.argtypes = [vp, C.c_int, C.c_int, C.c_double]
+    L.sensei_host_face_exchange.argtypes = [vp, C.c_int, C.c_int, dp, C.c_int]
+    L.sensei_hetero_workspace_size.argtypes = [C.POINTER(BlockDesc), C.POINTER(Scheme), C.c_int, C.POINTER(C.c_size_t)]
+    L.sensei_hetero_create.argtypes = [C.POINTER(BlockDesc), dp, C.POINTER(Scheme), C.POINTER(C.c_int), dp, C.c_int,
+                                       C.c_int, vp, C.c_size_t, vp, C.POINTER(vp)]
+    L.sensei_hetero_destroy.argtypes = [vp]
+    L.sensei_hetero_upload.argtypes = [vp, dp]
+    L.sensei_hetero_download.argtypes = [vp, dp]
+    L.sensei_hetero_step.argtypes = [vp, C.c_int, C.c_double, C.c_double, dp, dp]
     L.sensei_last_error.argtypes = []
     L.sensei_last_error.restype = C.c_char_p
     for name in EXPORTS[:-1]:
         getattr(L, name).restype = C.c_int
+    L.sensei_host_state.restype = dp
     _lib = L
     return L
 
@@ -223,6 +252,216 @@ def sensei_last_error() -> str:
 
 # ------------------------------------------------------------ convenience --
 
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def sensei_schedule(grid) -> dict:
+    v = [C.c_int() for _ in range(4)]
+    _check(load().sensei_schedule(grid, *[C.byref(x) for x in v]))
+    return {"kchunk": v[0].value, "persistent": bool(v[1].value), "order_by_cost": bool(v[2].value),
+            "ctas_per_sm": v[3].value}
+
+
+def sensei_rk_stage(grid, U_ptrs, rk, stage, dt, stream_ptr):
+    return _check(load().sensei_rk_stage(grid, _ptrs(U_ptrs), rk, stage, dt, stream_ptr))
+
+
+def sensei_face_exchange(grid, U_ptrs, block, stage, face, buf_ptr, unpack, stream_ptr):
+    return _check(load().sensei_face_exchange(grid, _ptrs(U_ptrs), block, stage, face, buf_ptr, int(unpack),
+                                              stream_ptr))
+
+
+def sensei_dt_min(grid, U_ptrs, cfl, stream_ptr) -> float:
+    out = C.c_double()
+    _check(load().sensei_dt_min(grid, _ptrs(U_ptrs), cfl, C.byref(out), stream_ptr))
+    return out.value
+
+
+def sensei_host_create(ni, nj, nk, nodes, scheme, threads):
+    out = C.c_void_p()
+    X = np.ascontiguousarray(nodes, dtype=np.float64)
+    _check(load().sensei_host_create(ni, nj, nk, _dptr(X), C.byref(scheme), threads, C.byref(out)))
+    return out.value
+
+
+def sensei_host_destroy(h):
+    return _check(load().sensei_host_destroy(h))
+
+
+def sensei_host_set_bc(h, face, bc_type, prim=None):
+    p = _dptr(np.ascontiguousarray(prim, dtype=np.float64)) if prim is not None else None
+    return _check(load().sensei_host_set_bc(h, face, bc_type, p))
+
+
+def sensei_host_layout(h) -> Layout:
+    lay = Layout()
+    _check(load().sensei_host_layout(h, C.byref(lay)))
+    return lay
+
+
+def sensei_host_state(h):
+    return load().sensei_host_state(h)
+
+
+def sensei_host_fill_ghosts(h):
+    return _check(load().sensei_host_fill_ghosts(h))
+
+
+def sensei_host_residual(h, R: np.ndarray):
+    return _check(load().sensei_host_residual(h, _dptr(R)))
+
+
+def sensei_host_dt_min(h, cfl) -> float:
+    out = C.c_double()
+    _check(load().sensei_host_dt_min(h, cfl, C.byref(out)))
+    return out.value
+
+
+def sensei_host_stage(h, rk, stage, dt):
+    return _check(load().sensei_host_stage(h, rk, stage, dt))
+
+
+def sensei_host_face_exchange(h, stage, face, buf: np.ndarray, unpack):
+    return _check(load().sensei_host_face_exchange(h, stage, face, _dptr(buf), int(unpack)))
+
+
+def sensei_hetero_workspace_size(block, scheme, nk_host) -> int:
+    n = C.c_size_t()
+    _check(load().sensei_hetero_workspace_size(C.byref(BlockDesc(*block)), C.byref(scheme), nk_host, C.byref(n)))
+    return n.value
+
+
+def sensei_hetero_create(block, nodes, scheme, bc_types, bc_prims, nk_host, threads, ws_ptr, ws_bytes, stream_ptr):
+    out = C.c_void_p()
+    X = np.ascontiguousarray(nodes, dtype=np.float64)
+    bt = (C.c_int * 6)(*bc_types)
+    bp = _dptr(np.ascontiguousarray(bc_prims, dtype=np.float64)) if bc_prims is not None else None
+    _check(load().sensei_hetero_create(C.byref(BlockDesc(*block)), _dptr(X), C.byref(scheme), bt, bp, nk_host,
+                                       threads, ws_ptr, ws_bytes, stream_ptr, C.byref(out)))
+    return out.value
+
+
+def sensei_hetero_destroy(h):
+    return _check(load().sensei_hetero_destroy(h))
+
+
+def sensei_hetero_upload(h, U: np.ndarray):
+    return _check(load().sensei_hetero_upload(h, _dptr(U)))
+
+
+def sensei_hetero_download(h, U: np.ndarray):
+    return _check(load().sensei_hetero_download(h, _dptr(U)))
+
+
+def sensei_hetero_step(h, rk, cfl, dt=0.0):
+    dt_used = C.c_double()
+    times = (C.c_double * 4)()
+    _check(load().sensei_hetero_step(h, rk, cfl, dt, C.byref(dt_used), times))
+    return dt_used.value, list(times)
+
+
+class HostBlock:
+    """Owner of one host-worker block (the host share of co-execution): its
+    state as a numpy view of the worker's own array."""
+
+    def __init__(self, dims, nodes, gamma=1.4, limiter=LIM_VANLEER, kappa=1.0 / 3.0, eps=1.0, entropy_fix=0.1,
+                 reconstruct_conserved=False, threads=1):
+        self.dims = tuple(dims)
+        ni, nj, nk = self.dims
+        self.scheme = Scheme(gamma=gamma, limiter=limiter, kappa=kappa, eps=eps, entropy_fix=entropy_fix,
+                             precision=FP64, reconstruct_conserved=int(reconstruct_conserved), mu=0.0, prandtl=0.72)
+        self.handle = sensei_host_create(ni, nj, nk, nodes, self.scheme, threads)
+        self.layout = sensei_host_layout(self.handle)
+        ptr = sensei_host_state(self.handle)
+        self.U = np.ctypeslib.as_array(ptr, shape=(self.layout.elems,))
+
+    def interior(self):
+        ni, nj, nk = self.dims
+        L = self.layout
+        return np.lib.stride_tricks.as_strided(self.U[L.offset:], shape=(5, nk, nj, ni),
+                                               strides=(8 * L.stride_var, 8 * L.stride_k, 8 * L.stride_j, 8))
+
+    def set_bc(self, face, bc_type, prim=None):
+        sensei_host_set_bc(self.handle, face, bc_type, prim)
+
+    def residual(self):
+        ni, nj, nk = self.dims
+        R = np.zeros((5, nk, nj, ni))
+        sensei_host_residual(self.handle, R)
+        return R
+
+    def dt_min(self, cfl):
+        return sensei_host_dt_min(self.handle, cfl)
+
+    def step(self, rk, dt):
+        for s in range(RK_STAGES[rk]):
+            sensei_host_stage(self.handle, rk, s, dt)
+
+    def close(self):
+        if self.handle:
+            sensei_host_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+RK_STAGES = {RK2_SSP: 2, RK3_SSP: 3, RK4_SSP2: 4}
+
+
+class Hetero:
+    """Owner of a co-execution driver (one block; the last nk_host k-planes
+    on host threads, the rest on the GPU) and its device workspace."""
+
+    def __init__(self, dims, nodes, bcs, nk_host, threads, gamma=1.4, limiter=LIM_VANLEER, kappa=1.0 / 3.0,
+                 eps=1.0, entropy_fix=0.1, reconstruct_conserved=False):
+        import torch
+        self.torch = torch
+        self.dims = tuple(dims)
+        self.scheme = Scheme(gamma=gamma, limiter=limiter, kappa=kappa, eps=eps, entropy_fix=entropy_fix,
+                             precision=FP64, reconstruct_conserved=int(reconstruct_conserved), mu=0.0, prandtl=0.72)
+        nbytes = sensei_hetero_workspace_size(self.dims, self.scheme, nk_host)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.ws.data_ptr()
+        wsp = (base + 255) // 256 * 256
+        types = [bc[0] for bc in bcs]
+        prims = np.zeros((6, 5))
+        for f, bc in enumerate(bcs):
+            if bc[1] is not None:
+                prims[f] = bc[1]
+        self.stream = torch.cuda.current_stream()
+        self.handle = sensei_hetero_create(self.dims, nodes, self.scheme, types, prims, nk_host, threads, wsp,
+                                           nbytes, self.stream.cuda_stream)
+
+    def upload(self, U):
+        sensei_hetero_upload(self.handle, np.ascontiguousarray(U, dtype=np.float64))
+
+    def download(self):
+        ni, nj, nk = self.dims
+        U = np.zeros((5, nk, nj, ni))
+        sensei_hetero_download(self.handle, U)
+        return U
+
+    def step(self, rk=RK3_SSP, cfl=0.5, dt=0.0):
+        return sensei_hetero_step(self.handle, rk, cfl, dt)
+
+    def close(self):
+        if self.handle:
+            sensei_hetero_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class StepGraph:
     def __init__(self, handle, grid):
         self.handle = handle
@@ -327,6 +566,9 @@ class Grid:
 
     def autotune(self, Us):
         return sensei_autotune(self.handle, [U.data_ptr() for U in Us], self.sptr)
+
+    def schedule(self):
+        return sensei_schedule(self.handle)
 
     def debug_set(self, key, value):
         sensei_debug_set(self.handle, key, value)

@@ -23,7 +23,7 @@ def sensei():
 def _declared():
     with open(os.path.join(ROOT, "include", "sensei.h")) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^(?:sensei_status|const char \*)\s*(sensei_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^(?:sensei_status|const char \*|double \*)\s*(sensei_\w+)\s*\(", text, re.M)))
 
 
 def test_every_declared_symbol_is_exported(sensei):
