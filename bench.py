@@ -106,9 +106,11 @@ def alg_bytes_per_cell(form, stage, two_d, stages=3):
 # DRAM bytes per interior cell and stencil launch, averaged over the three
 # SSPRK3 stage launches, from ncu dram__bytes_read.sum + dram__bytes_write.sum
 # of the 192^3 case of the periodic 3D workload (profiles/
-# stencil_traffic_periodic3d_192.md); the same tile schedule at 256^3, so the
-# traffic scales with the cells.  Re-measure when the kernel changes.
-MEASURED_TRAFFIC_B_PER_CELL = {"fp64": 226.6, "fp32_flux": 180.8}
+# stencil_traffic_periodic3d_192.md for FP64, profiles/
+# stencil32p_traffic_periodic3d_192.md for the FP32 flux form); the same tile
+# schedule at 256^3, so the traffic scales with the cells.  Re-measure when
+# the kernel changes.
+MEASURED_TRAFFIC_B_PER_CELL = {"fp64": 226.6, "fp32_flux": 192.1}
 
 
 def measured_peaks():
@@ -798,7 +800,7 @@ def main():
             "traffic": None if two_d else MEASURED_TRAFFIC_B_PER_CELL["fp32_flux"] * cells,
             "traffic_source": "ncu DRAM bytes per cell of the 192^3 capture x cells (3-stage average)",
             "peak_source": peak_src,
-            "kernel": "stencil32_kernel<double> (FP32 MUSCL + Roe on the FP64 state, FP64 update)",
+            "kernel": "stencil32p_kernel<double> (paired FP32 MUSCL + Roe on the FP64 state, FP64 update)",
             "alg_bytes_per_launch": byts, "kernel_ms_per_launch": per_launch_ms,
             "pipe": pipe_roofline(form, step_flops_per_launch(w.limiter, two_d, cells, stages), per_launch_ms),
         }
