@@ -249,7 +249,8 @@ sensei_status sensei_step_graph_launch(sensei_step_graph *graph, sensei_stream s
 sensei_status sensei_step_graph_destroy(sensei_step_graph *graph);
 
 /* Pick the work schedule of the batched stencil launches by timing them
- * on this grid and the states U (dt = 0 first-stage launches into the stage
+ * on this grid and the states U (the launches of a three-stage step with
+ * dt = 0 -- a first stage from U and two later stages -- into the stage
  * buffers; U's ghosts are refilled, its interior untouched): the k-extent of
  * a work item (tile of 32 x 8 cells x kchunk planes) and persistent CTAs
  * (resident CTAs x SMs, items taken round-robin) versus one CTA per item.
@@ -412,9 +413,11 @@ sensei_status sensei_residual_norms_noalloc(const double *R, int ni, int nj, int
  *   SENSEI_DEBUG_TX_EXTRA: bytes added to every tile phase's expected count
  *     (0 = none).  A positive value makes every such wait run out: the data
  *     arrives, the phase never completes.  For tests only.
+ *   SENSEI_DEBUG_ITEM_ORDER: 0 block-major work items, 1 by descending cost
+ *     (the autotuner's two orders; for tests that compare them).
  * Apply to the following launches of this grid.  SENSEI_ERR_INVALID_ARG for
  * an unknown key or a negative value. */
-enum { SENSEI_DEBUG_WAIT_LIMIT = 1, SENSEI_DEBUG_TX_EXTRA = 2 };
+enum { SENSEI_DEBUG_WAIT_LIMIT = 1, SENSEI_DEBUG_TX_EXTRA = 2, SENSEI_DEBUG_ITEM_ORDER = 3 };
 sensei_status sensei_debug_set(sensei_grid *grid, int key, long long value);
 
 /* Message of the last failing call on this thread ("" if none). */

@@ -750,6 +750,10 @@ sensei_status sensei_debug_set(sensei_grid *grid, int key, long long value)
     } else if (key == SENSEI_DEBUG_TX_EXTRA) {
         if (value > (1 << 16)) return fail(SENSEI_ERR_INVALID_ARG, "tx_extra above 65536 bytes");
         grid->tx_extra = (unsigned)value;
+    } else if (key == SENSEI_DEBUG_ITEM_ORDER) {
+        if (value > 1) return fail(SENSEI_ERR_INVALID_ARG, "item order 0 or 1");
+        grid->order_mode = (int)value;
+        grid->dirty = true;
     } else {
         return fail(SENSEI_ERR_INVALID_ARG, "unknown debug key %d", key);
     }
@@ -1253,11 +1257,15 @@ sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk_o
     st = prepare_step(grid, U, s);
     if (st == SENSEI_OK) st = fill_slot(grid, SLOT_USER, U, s);
     if (st != SENSEI_OK) return st;
-    // first-stage launches with dt = 0 into the stage buffers: they time the
-    // stencil without touching the caller's state
+    // the stage launches of a three-stage step with dt = 0 into the stage
+    // buffers: a first stage (the caller's state in, norm partials) and twice
+    // a later stage (a stage state in, blended with U^n); the first and the
+    // later stages are different kernels in the FP32-storage form and
+    // different instantiations in the others, and their best schedules can
+    // differ.  Nothing of the caller's state is written.
     CUDA_TRY(launch_set_scalar(grid->dt_slot, 0.0, s));
     const bool incr = incr_mode(grid);
-    StencilCall c;
+    StencilCall c, c2;
     memset(&c, 0, sizeof c);
     c.mode = incr ? MODE_INCR : MODE_ACCUM;
     c.in_slot = SLOT_USER;
@@ -1269,6 +1277,17 @@ sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk_o
     c.dt_slot = grid->dt_slot;
     c.dt_scale = 1.0;
     c.user = U;
+    c.partials = true;
+    c.push = 1;
+    c2 = c;
+    c2.partials = false;
+    c2.in_slot = incr ? SLOT_X0 : SLOT_ST0;
+    c2.out_slot = incr ? SLOT_X1 : SLOT_ST1;
+    c2.alpha = 0.75;
+    c2.beta = 0.25;
+    c2.gdt = 0.25;
+    c2.dprev = incr ? 0 : -1;
+    c2.dout = incr ? 1 : -1;
     int max_nk = 1;
     for (auto &H : grid->plan.blocks) max_nk = std::max(max_nk, H.dev.nk);
     cudaEvent_t e0, e1;
@@ -1296,6 +1315,7 @@ sensei_status sensei_autotune(sensei_grid *grid, double *const *U, int *kchunk_o
             for (int rep = 0; rep < 3 && st == SENSEI_OK; ++rep) {
                 cudaEventRecord(e0, s);
                 st = stencil_launch(grid, c, s);
+                for (int later = 0; later < 2 && st == SENSEI_OK; ++later) st = stencil_launch(grid, c2, s);
                 cudaEventRecord(e1, s);
                 if (st == SENSEI_OK && cudaEventSynchronize(e1) != cudaSuccess)
                     st = fail(SENSEI_ERR_CUDA, "autotune timing failed");

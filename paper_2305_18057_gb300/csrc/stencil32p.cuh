@@ -118,11 +118,15 @@ __device__ __forceinline__ int halo_cell(int t)
     return r * TW + c;
 }
 
-template <typename TS, int LIM>
+// PART: the launch accumulates the norm partials (the first stage of a
+// step, or a residual); a separate instantiation, so that the other stages
+// do not hold the accumulators' registers
+template <typename TS, int LIM, bool PART>
 __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_constant__ BatchParams<float> p)
 {
     using SM = SmemP<TS>;
     constexpr bool WIDE = sizeof(TS) == 8;   // FP64 stage input: the only case that computes norms
+    constexpr bool NORMS = WIDE && PART;
     extern __shared__ __align__(128) unsigned char smem[];
     TS *sRaw = reinterpret_cast<TS *>(smem + SM::off_raw);
     auto rawbuf = [&](int n) { return reinterpret_cast<TS *>(smem + SM::off_raw + n * SM::raw_buf); };
@@ -413,7 +417,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
             const long long cell = cell0 + (long long)k * L.sk;
             const long long mc = (long long)k * ml.mplane + (long long)cj * ml.mpitch + ci;
             if (!warm && col_valid) {
-                const bool want_in = WIDE && (p.mode == MODE_ACCUM || p.partials || (p.mode == MODE_INCR && !out_wide));
+                const bool want_in = WIDE && (p.mode == MODE_ACCUM || NORMS || (p.mode == MODE_INCR && !out_wide));
                 const double *ind = reinterpret_cast<const double *>(in);
                 const float *dprev = p.dprev >= 0 ? B.ds[p.dprev] : nullptr;
                 const double *un = p.user[b];
@@ -425,7 +429,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                 }
                 if (p.local) dtvd = B.dtv[mc];
                 else if (p.mode == MODE_ACCUM) ivd = B.ivol[mc];
-                if (WIDE && p.partials) vold = B.vol[mc];
+                if (NORMS) vold = B.vol[mc];
             }
             if (__syncthreads_or(!ok)) {
                 // the copies this CTA has in flight (this slot's, if it is
@@ -453,7 +457,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                 if (p.dprev >= 0) prefetch_lines(B.ds[p.dprev] + row0 - 2, L.sj * 4, nrow_in, L.sv * 4, NV, len * 4, t);
                 if (p.mode == MODE_ACCUM && !p.local)
                     prefetch_lines(B.ivol + m0, ml.mpitch * 8, nrow_in, 0, 1, row64, t);
-                if (WIDE && p.partials) prefetch_lines(B.vol + m0, ml.mpitch * 8, nrow_in, 0, 1, row64, t);
+                if (NORMS) prefetch_lines(B.vol + m0, ml.mpitch * 8, nrow_in, 0, 1, row64, t);
             }
 
             if (warm) {
@@ -539,7 +543,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                     }
                     if (p.push && boundary && p.mode != MODE_RESIDUAL) push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
                 }
-                if (WIDE && p.partials) {
+                if (NORMS) {
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         // r exactly as hi + lo: the FP32 residual, or with a
@@ -561,7 +565,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
         if (failed) break;
 
         // ---- norm partials of this item, fixed-order reduction in FP64
-        if (WIDE && p.partials) {
+        if (NORMS) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 double a = (double)nsq_hi[v] + (double)nsq_lo[v], bm = (double)nmax[v], cc = ncons[v];
@@ -594,12 +598,20 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
 template <typename TS>
 struct Stencil32PLauncher {
     using Fn = void (*)(const BatchParams<float>);
-    static Fn pick(int limiter)
+    static Fn pick(int limiter, bool part)
     {
+        // norm partials only from an FP64 stage input
+        if (part && sizeof(TS) == 8) {
+            switch (limiter) {
+            case SENSEI_LIM_NONE: return stencil32p_kernel<TS, SENSEI_LIM_NONE, true>;
+            case SENSEI_LIM_MINMOD: return stencil32p_kernel<TS, SENSEI_LIM_MINMOD, true>;
+            default: return stencil32p_kernel<TS, SENSEI_LIM_VANLEER, true>;
+            }
+        }
         switch (limiter) {
-        case SENSEI_LIM_NONE: return stencil32p_kernel<TS, SENSEI_LIM_NONE>;
-        case SENSEI_LIM_MINMOD: return stencil32p_kernel<TS, SENSEI_LIM_MINMOD>;
-        default: return stencil32p_kernel<TS, SENSEI_LIM_VANLEER>;
+        case SENSEI_LIM_NONE: return stencil32p_kernel<TS, SENSEI_LIM_NONE, false>;
+        case SENSEI_LIM_MINMOD: return stencil32p_kernel<TS, SENSEI_LIM_MINMOD, false>;
+        default: return stencil32p_kernel<TS, SENSEI_LIM_VANLEER, false>;
         }
     }
     static cudaError_t prepare(Fn fn)
@@ -610,19 +622,25 @@ struct Stencil32PLauncher {
     }
     static cudaError_t launch(const BatchParams<float> &p, int limiter, int grid, cudaStream_t s)
     {
-        Fn fn = pick(limiter);
+        Fn fn = pick(limiter, p.partials != nullptr);
         cudaError_t e = prepare(fn);
         if (e != cudaSuccess) return e;
         fn<<<grid, NTHREADS, SmemP<TS>::bytes, s>>>(p);
         return cudaGetLastError();
     }
+    // the smaller of the two instantiations' resident CTAs per SM
     static int ctas_per_sm(int limiter)
     {
-        Fn fn = pick(limiter);
-        if (prepare(fn) != cudaSuccess) return 0;
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NTHREADS, SmemP<TS>::bytes) != cudaSuccess) return 0;
-        return n;
+        int best = 1 << 30;
+        for (int part = 0; part < 2; ++part) {
+            Fn fn = pick(limiter, part != 0);
+            if (prepare(fn) != cudaSuccess) return 0;
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NTHREADS, SmemP<TS>::bytes) != cudaSuccess)
+                return 0;
+            best = n < best ? n : best;
+        }
+        return best;
     }
 };
 

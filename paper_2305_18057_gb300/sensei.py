@@ -229,7 +229,7 @@ def sensei_profile_read(grid, reset=True):
     return ms.value, ns.value, nk.value
 
 
-DEBUG_WAIT_LIMIT, DEBUG_TX_EXTRA = 1, 2
+DEBUG_WAIT_LIMIT, DEBUG_TX_EXTRA, DEBUG_ITEM_ORDER = 1, 2, 3
 
 
 def sensei_debug_set(grid, key, value):

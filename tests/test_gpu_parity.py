@@ -251,3 +251,25 @@ def test_local_time_stepping_converges_on_gpu():
         # FP64 reaches round-off, the double-float form nearly (48 bits); the
         # FP32-flux forms stall at their own rounding level
         assert l2 < {0: 1e-9, 3: 1e-8}.get(prec, 1e-4) * l2_0, (prec, l2 / l2_0)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_item_order_changes_no_result(precision):
+    """Work items by descending cost (the order the autotuner may choose for
+    uneven blocks) give bitwise the block-major results, norms included."""
+    from paper_2305_18057_gb300 import sensei
+    w = CASES["lattice"]()
+    runs = []
+    for order in (0, 1):
+        g = gpu_grid(w, precision=precision)
+        Us = gpu_states(g, w)
+        g.debug_set(sensei.DEBUG_ITEM_ORDER, order)
+        for _ in range(5):
+            g.rk_step(Us, RK["rk3"], cfl=0.5)
+        _, l2, linf, cons = g.norms()
+        assert g.schedule()["order_by_cost"] == bool(order)
+        runs.append(([g.download(U, b) for b, U in enumerate(Us)], l2, linf, cons))
+    for a, b in zip(runs[0][0], runs[1][0]):
+        np.testing.assert_array_equal(a, b)
+    for x, y in zip(runs[0][1:], runs[1][1:]):
+        np.testing.assert_array_equal(x, y)
