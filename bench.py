@@ -412,14 +412,37 @@ def lattice_variant(args, peaks, peak_src, world):
     per step, autotuned schedule; beside it the plain FP64 form on the same
     lattice (its speedup) and the density error against it after the same
     steps from the same state."""
+    from paper_2305_18057_gb300 import workloads as wl
+    out = workload_variant(args, peaks, peak_src, world, wl.lattice_3d(), "fp32_flux", max(3, min(args.steps, 10)))
+    out["workload"] = WORKLOADS["c4"]
+    return out
+
+
+def ramp_variant(args, peaks, peak_src, world):
+    """The 512^3 Mach-4 ramp (one block, wall / inflow / outflow rules,
+    stretched grid) inside the default run: the FP32-storage form, a CUDA
+    graph per step, autotuned schedule; beside it the FP64 form (its speedup
+    and the density error against it)."""
+    from paper_2305_18057_gb300 import workloads as wl
+    out = workload_variant(args, peaks, peak_src, world, wl.ramp_3d(n=512), "fp32_store", 5)
+    out["workload"] = WORKLOADS["c5"]
+    return out
+
+
+def workload_variant(args, peaks, peak_src, world, w, form, steps):
+    """One mixed-precision form on workload w: CUDA-graph steps with the
+    autotuned schedule, its stencil roofline, and the FP64 form on the same
+    workload (speedup, density error after the same steps from the same
+    state)."""
     import torch
-    from paper_2305_18057_gb300 import sensei, workloads as wl
-    w = wl.lattice_3d()
+    from paper_2305_18057_gb300 import sensei
     cells, stages, rk = w.cells, 3, sensei.RK3_SSP
-    steps = max(3, min(args.steps, 10))
     res = {}
     states = {}
-    for name, prec in (("fp64", sensei.FP64), ("fp32_flux", sensei.FP32_FLUX)):
+    precs = {"fp32_flux": sensei.FP32_FLUX, "fp32_store": sensei.FP32_STORE}
+    kernels = {"fp32_flux": "stencil32p_kernel<double> (paired FP32 MUSCL + Roe on the FP64 state)",
+               "fp32_store": "stencil32p_kernel<float> / <double> (paired FP32 MUSCL + Roe, FP32 stage states)"}
+    for name, prec in (("fp64", sensei.FP64), (form, precs[form])):
         g, Us, sched = gpu_setup(w, prec)
         for _ in range(args.warmup):
             g.rk_step(Us, rk, cfl=w.cfl)
@@ -430,14 +453,14 @@ def lattice_variant(args, peaks, peak_src, world):
         r = {"value": cells * stages * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
              "schedule": g.schedule(), "kernel_ms_per_launch": per_launch,
              "steps": steps, "step": "cuda graph per step"}
-        if name == "fp32_flux":
-            byts = cells * sum(alg_bytes_per_cell("fp32_flux", s_, False) for s_ in range(stages)) / stages
+        if name == form:
+            byts = cells * sum(alg_bytes_per_cell(form, s_, False) for s_ in range(stages)) / stages
             hbm = byts / (per_launch / 1e3) / 1e9
             r["roofline"] = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": hbm / peaks["hbm_gbs"], "peak_source": peak_src,
-                             "kernel": "stencil32p_kernel<double> (paired FP32 MUSCL + Roe on the FP64 state)",
+                             "kernel": kernels[form],
                              "alg_bytes_per_launch": byts, "kernel_ms_per_launch": per_launch,
-                             "pipe": pipe_roofline("fp32_flux", step_flops_per_launch(w.limiter, False, cells, stages),
+                             "pipe": pipe_roofline(form, step_flops_per_launch(w.limiter, False, cells, stages),
                                                    per_launch)}
         res[name] = r
         # the same number of steps from the initial state for the error
@@ -450,12 +473,12 @@ def lattice_variant(args, peaks, peak_src, world):
         del g, Us
         torch.cuda.empty_cache()
     num = math.sqrt(sum(float(torch.linalg.vector_norm(a - b_)) ** 2
-                        for a, b_ in zip(states["fp32_flux"], states["fp64"])))
+                        for a, b_ in zip(states[form], states["fp64"])))
     den = math.sqrt(sum(float(torch.linalg.vector_norm(b_)) ** 2 for b_ in states["fp64"]))
-    out = dict(res["fp32_flux"])
+    out = dict(res[form])
     out.update({
-        "workload": WORKLOADS["c4"], "cells": cells, "blocks": len(w.dims), "precision": "fp32_flux",
-        "speedup_vs_fp64": (res["fp32_flux"]["value"] / res["fp64"]["value"]) if world == 1 else None,
+        "cells": cells, "blocks": len(w.dims), "precision": form,
+        "speedup_vs_fp64": (res[form]["value"] / res["fp64"]["value"]) if world == 1 else None,
         "rho_l2_rel_err_vs_fp64": num / den, "steps_compared": steps,
         "fp64": res["fp64"]})
     return out
@@ -707,6 +730,14 @@ def oracle_leg(args, w, line, main_prec):
             t["sample"] += "; the lattice's state with seeded 5% perturbations"
         line["variants"]["c4_lattice"]["err_vs_oracle"] = t4["fp32_flux"]
         line["variants"]["c4_lattice"]["fp64"]["err_vs_oracle"] = t4["fp64"]
+    if "c5_ramp" in line.get("variants", {}):
+        # the ramp's uniform inflow likewise: seeded 5% perturbations
+        from paper_2305_18057_gb300 import workloads as wl
+        t5 = err_vs_oracle(wl.ramp_3d(n=512, perturb=0.05), [("fp64", sensei.FP64), ("fp32_store", sensei.FP32_STORE)])
+        for t in t5.values():
+            t["sample"] += "; the ramp's state with seeded 5% perturbations"
+        line["variants"]["c5_ramp"]["err_vs_oracle"] = t5["fp32_store"]
+        line["variants"]["c5_ramp"]["fp64"]["err_vs_oracle"] = t5["fp64"]
 
 
 # -------------------------------------------------------------------- main --
@@ -915,6 +946,8 @@ def main():
         del gv, Uv
         if args.workload != "c4":
             line["variants"]["c4_lattice"] = lattice_variant(args, peaks, peak_src, world)
+        if args.workload == "c3" and args.n is None:
+            line["variants"]["c5_ramp"] = ramp_variant(args, peaks, peak_src, world)
 
     # the performance model of Sec. 6 on this GPU: the 2D ramp at three N_l
     # with N_w = 1024, each cut into P = 1, 4, 16, 64 i-blocks (the model's

@@ -406,8 +406,10 @@ sensei_status sensei_residual_norms_noalloc(const double *R, int ni, int nj, int
  * they exist so that failure detection can be tested without a GPU fault).
  * The FP32 stencil waits on mbarriers for its bulk tile copies; every wait
  * gives up after a limit, sets the device error word, waits once more for
- * the copies in flight and leaves, and sensei_norms then returns
- * SENSEI_ERR_TIMEOUT.
+ * the copies in flight (bounded too) and leaves, and sensei_norms then
+ * returns SENSEI_ERR_TIMEOUT.  If that second wait also gives up, the CTA
+ * leaves with a copy into its shared memory still pending: after a genuine
+ * timeout treat the run's later results as unsound.
  *   SENSEI_DEBUG_WAIT_LIMIT: the limit in SM clock cycles (0 = the default
  *     2^31, about a second).
  *   SENSEI_DEBUG_TX_EXTRA: bytes added to every tile phase's expected count

@@ -120,8 +120,11 @@ __device__ __forceinline__ int halo_cell(int t)
 
 // PART: the launch accumulates the norm partials (the first stage of a
 // step, or a residual); a separate instantiation, so that the other stages
-// do not hold the accumulators' registers
-template <typename TS, int LIM, bool PART>
+// do not hold the accumulators' registers.  MODE: the launch's update
+// (MODE_ACCUM, MODE_INCR or MODE_RESIDUAL, the BatchParams field it
+// replaces), fixed at compile time so that each instantiation carries only
+// its own update code and operands.
+template <typename TS, int LIM, bool PART, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_constant__ BatchParams<float> p)
 {
     using SM = SmemP<TS>;
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
              he = sp2(LIM == SENSEI_LIM_VANLEER ? 2.0f * p.half_eps : p.half_eps);
     const P2 fix = sp2(p.fix), ifix = sp2(p.ifix);
     const int cons = p.cons;
-    const bool update = p.mode != MODE_RESIDUAL;
+    const bool update = MODE != MODE_RESIDUAL;
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
     const float gdt_dt32 = (float)(p.gdt * dt);
     const float gdt32 = (float)p.gdt;
@@ -199,11 +202,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
         const TS *in = (p.in_slot == SLOT_X0 || p.in_slot == SLOT_X1)
                            ? reinterpret_cast<const TS *>(slot32(B, p.in_slot))
                            : reinterpret_cast<const TS *>(slot64(B, p.user[b], p.in_slot));
-        const bool out_wide = p.mode != MODE_RESIDUAL && p.out_slot < SLOT_X0;
+        const bool out_wide = MODE != MODE_RESIDUAL && p.out_slot < SLOT_X0;
         const int len = min(TW, (int)L.sj - i0);
         const long long rec_stride = (long long)B.tiles_i * B.tiles_j * REC;
         const float *rec0 = B.rec32 + ((long long)tile_j * B.tiles_i + tile_i) * REC;
-        const bool need_un = (p.mode == MODE_ACCUM && p.alpha != 0.0) || (p.mode == MODE_INCR && (out_wide || !WIDE));
+        const bool need_un = (MODE == MODE_ACCUM && p.alpha != 0.0) || (MODE == MODE_INCR && (out_wide || !WIDE));
         // the update's per-cell operands, prefetched into L2 two planes ahead
         // (rows of the tile's interior: FP64 from cell i0, FP32 from i0 - 2,
         // so that every row start is 16-byte aligned)
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
             const long long cell = cell0 + (long long)k * L.sk;
             const long long mc = (long long)k * ml.mplane + (long long)cj * ml.mpitch + ci;
             if (!warm && col_valid) {
-                const bool want_in = WIDE && (p.mode == MODE_ACCUM || NORMS || (p.mode == MODE_INCR && !out_wide));
+                const bool want_in = WIDE && (MODE == MODE_ACCUM || NORMS || (MODE == MODE_INCR && !out_wide));
                 const double *ind = reinterpret_cast<const double *>(in);
                 const float *dprev = p.dprev >= 0 ? B.ds[p.dprev] : nullptr;
                 const double *un = p.user[b];
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                     dpv[v] = dprev ? dprev[cell + v * L.sv] : 0.0f;
                 }
                 if (p.local) dtvd = B.dtv[mc];
-                else if (p.mode == MODE_ACCUM) ivd = B.ivol[mc];
+                else if (MODE == MODE_ACCUM) ivd = B.ivol[mc];
                 if (NORMS) vold = B.vol[mc];
             }
             if (__syncthreads_or(!ok)) {
@@ -455,7 +458,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                 const long long m0 = (long long)c * ml.mplane + (long long)j0 * ml.mpitch + i0;
                 if (need_un) prefetch_lines(p.user[b] + row0, L.sj * 8, nrow_in, L.sv * 8, NV, row64, t);
                 if (p.dprev >= 0) prefetch_lines(B.ds[p.dprev] + row0 - 2, L.sj * 4, nrow_in, L.sv * 4, NV, len * 4, t);
-                if (p.mode == MODE_ACCUM && !p.local)
+                if (MODE == MODE_ACCUM && !p.local)
                     prefetch_lines(B.ivol + m0, ml.mpitch * 8, nrow_in, 0, 1, row64, t);
                 if (NORMS) prefetch_lines(B.vol + m0, ml.mpitch * 8, nrow_in, 0, 1, row64, t);
             }
@@ -489,7 +492,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                 const long long rc = ((long long)k * B.nj + cj) * B.ni + ci;
                 const bool boundary =
                     ci < 2 || ci >= B.ni - 2 || cj < 2 || cj >= B.nj - 2 || k < 2 || k >= B.nk - 2;
-                if (p.mode == MODE_INCR) {
+                if (MODE == MODE_INCR) {
                     // FP32 increment D = beta Dprev - gdt dt/|Omega| R; X = float(U^n) + D,
                     // or on the last stage U^n + D in FP64
                     const float c32 = p.local ? gdt32 * to_f32(dtvd) : gdt_dt32 * ivol;
@@ -525,14 +528,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                         if (p.push && boundary) push_ghosts<float>(p, B, b, ci, cj, k, q32, NFACES);
                     }
                 } else {
-                    const double coef = p.mode != MODE_ACCUM ? 0.0 : p.local ? -p.gdt * dtvd : -p.gdt * dt * ivd;
+                    const double coef = MODE != MODE_ACCUM ? 0.0 : p.local ? -p.gdt * dtvd : -p.gdt * dt * ivd;
                     double q64[NV];
                     double *out64 = out_wide ? slot64(B, p.user[b], p.out_slot) : nullptr;
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         double r = to_f64(rres[v]);
-                        if (p.mode == MODE_RESIDUAL && p.src[b]) r -= p.src[b][v * nint + rc];
-                        if (p.mode == MODE_ACCUM) {
+                        if (MODE == MODE_RESIDUAL && p.src[b]) r -= p.src[b][v * nint + rc];
+                        if (MODE == MODE_ACCUM) {
                             double val = p.beta * uin[v] + coef * r;
                             if (p.alpha != 0.0) val += p.alpha * unv[v];
                             out64[cell + v * L.sv] = val;
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                             p.rout[b][v * nint + rc] = r;
                         }
                     }
-                    if (p.push && boundary && p.mode != MODE_RESIDUAL) push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
+                    if (p.push && boundary && MODE != MODE_RESIDUAL) push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
                 }
                 if (NORMS) {
 #pragma unroll
@@ -549,7 +552,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                         // r exactly as hi + lo: the FP32 residual, or with a
                         // source term its FP64 value split in two floats
                         float hi = rres[v], lo = 0.0f;
-                        if (p.mode == MODE_RESIDUAL && p.src[b]) {
+                        if (MODE == MODE_RESIDUAL && p.src[b]) {
                             const double r = to_f64(rres[v]) - p.src[b][v * nint + rc];
                             hi = to_f32(r);
                             lo = to_f32(r - to_f64(hi));
@@ -598,20 +601,30 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
 template <typename TS>
 struct Stencil32PLauncher {
     using Fn = void (*)(const BatchParams<float>);
-    static Fn pick(int limiter, bool part)
+    template <int LIM>
+    static Fn pick_lim(bool part, int mode)
     {
-        // norm partials only from an FP64 stage input
-        if (part && sizeof(TS) == 8) {
-            switch (limiter) {
-            case SENSEI_LIM_NONE: return stencil32p_kernel<TS, SENSEI_LIM_NONE, true>;
-            case SENSEI_LIM_MINMOD: return stencil32p_kernel<TS, SENSEI_LIM_MINMOD, true>;
-            default: return stencil32p_kernel<TS, SENSEI_LIM_VANLEER, true>;
-            }
+        if (sizeof(TS) == 4) {
+            // an FP32 stage input exists only in the later FP32-storage stages
+            return mode == MODE_INCR && !part ? stencil32p_kernel<TS, LIM, false, MODE_INCR> : nullptr;
         }
+        switch (mode) {
+        case MODE_ACCUM:
+            return part ? stencil32p_kernel<TS, LIM, true, MODE_ACCUM> : stencil32p_kernel<TS, LIM, false, MODE_ACCUM>;
+        case MODE_INCR:
+            return part ? stencil32p_kernel<TS, LIM, true, MODE_INCR> : stencil32p_kernel<TS, LIM, false, MODE_INCR>;
+        case MODE_RESIDUAL:
+            return part ? stencil32p_kernel<TS, LIM, true, MODE_RESIDUAL>
+                        : stencil32p_kernel<TS, LIM, false, MODE_RESIDUAL>;
+        default: return nullptr;
+        }
+    }
+    static Fn pick(int limiter, bool part, int mode)
+    {
         switch (limiter) {
-        case SENSEI_LIM_NONE: return stencil32p_kernel<TS, SENSEI_LIM_NONE, false>;
-        case SENSEI_LIM_MINMOD: return stencil32p_kernel<TS, SENSEI_LIM_MINMOD, false>;
-        default: return stencil32p_kernel<TS, SENSEI_LIM_VANLEER, false>;
+        case SENSEI_LIM_NONE: return pick_lim<SENSEI_LIM_NONE>(part, mode);
+        case SENSEI_LIM_MINMOD: return pick_lim<SENSEI_LIM_MINMOD>(part, mode);
+        default: return pick_lim<SENSEI_LIM_VANLEER>(part, mode);
         }
     }
     static cudaError_t prepare(Fn fn)
@@ -622,25 +635,30 @@ struct Stencil32PLauncher {
     }
     static cudaError_t launch(const BatchParams<float> &p, int limiter, int grid, cudaStream_t s)
     {
-        Fn fn = pick(limiter, p.partials != nullptr);
+        // norm partials only from an FP64 stage input
+        Fn fn = pick(limiter, sizeof(TS) == 8 && p.partials != nullptr, p.mode);
+        if (!fn) return cudaErrorInvalidValue;
         cudaError_t e = prepare(fn);
         if (e != cudaSuccess) return e;
         fn<<<grid, NTHREADS, SmemP<TS>::bytes, s>>>(p);
         return cudaGetLastError();
     }
-    // the smaller of the two instantiations' resident CTAs per SM
+    // the smallest resident CTAs per SM over the instantiations of this
+    // stage input
     static int ctas_per_sm(int limiter)
     {
         int best = 1 << 30;
-        for (int part = 0; part < 2; ++part) {
-            Fn fn = pick(limiter, part != 0);
-            if (prepare(fn) != cudaSuccess) return 0;
-            int n = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NTHREADS, SmemP<TS>::bytes) != cudaSuccess)
-                return 0;
-            best = n < best ? n : best;
-        }
-        return best;
+        for (int mode : {MODE_ACCUM, MODE_INCR, MODE_RESIDUAL})
+            for (int part = 0; part < 2; ++part) {
+                Fn fn = pick(limiter, part != 0, mode);
+                if (!fn) continue;
+                if (prepare(fn) != cudaSuccess) return 0;
+                int n = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NTHREADS, SmemP<TS>::bytes) != cudaSuccess)
+                    return 0;
+                best = n < best ? n : best;
+            }
+        return best == (1 << 30) ? 0 : best;
     }
 };
 

@@ -1,7 +1,7 @@
 // stencil_f32p.cu -- the 3D FP32-arithmetic stencil kernel with paired face
-// fluxes (stencil32p.cuh), on an FP64 stage input (FP32 flux on the FP64
-// state; the first FP32-storage stage; residuals) and on an FP32 stage state
-// (the later FP32-storage stages), for every limiter.
+// fluxes (stencil32p.cuh) on an FP32 stage state (the later FP32-storage
+// stages), for every limiter; the tensor maps of the state slots; the
+// dispatch between this and the FP64-input kernel (stencil_f32pd.cu).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -52,14 +52,16 @@ bool encode_state_map(void *out, const void *base, const BlockDev &B, bool f32)
     return r == CUDA_SUCCESS;
 }
 
+// the FP32-stage-state instantiations here, the FP64-input ones in
+// stencil_f32pd.cu (two translation units that compile in parallel)
 cudaError_t launch_stencil32p(const BatchParams<float> &p, int limiter, bool in_f32, int grid, cudaStream_t s)
 {
     if (in_f32) return Stencil32PLauncher<float>::launch(p, limiter, grid, s);
-    return Stencil32PLauncher<double>::launch(p, limiter, grid, s);
+    return launch_stencil32p_f64in(p, limiter, grid, s);
 }
 
 int stencil32p_ctas_per_sm(int limiter, bool in_f32)
 {
-    return in_f32 ? Stencil32PLauncher<float>::ctas_per_sm(limiter) : Stencil32PLauncher<double>::ctas_per_sm(limiter);
+    return in_f32 ? Stencil32PLauncher<float>::ctas_per_sm(limiter) : stencil32p_ctas_per_sm_f64in(limiter);
 }
 }  // namespace sensei
