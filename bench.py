@@ -283,9 +283,16 @@ def time_steps(g, Us, steps, rk, cfl, profile=False):
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    prof = g.profile_read(reset=True) if profile else None
+    prof = None
     if profile:
+        # stencil launch times by Runge-Kutta stage (the grid's launches cycle
+        # through the stages in order)
+        per = g.profile_launches()
+        st_ms, st_n, k_n = g.profile_read(reset=True)
         g.profile(False)
+        nst = len(per) // max(steps, 1)
+        by_stage = [sum(per[i::nst]) / len(per[i::nst]) for i in range(nst)] if nst else []
+        prof = (st_ms, st_n, k_n, by_stage)
     return ms, prof
 
 
@@ -460,6 +467,7 @@ def workload_variant(args, peaks, peak_src, world, w, form, steps):
                              "frac": hbm / peaks["hbm_gbs"], "peak_source": peak_src,
                              "kernel": kernels[form],
                              "alg_bytes_per_launch": byts, "kernel_ms_per_launch": per_launch,
+                             "kernel_ms_by_stage": prof[3],
                              "pipe": pipe_roofline(form, step_flops_per_launch(w.limiter, False, cells, stages),
                                                    per_launch)}
         res[name] = r
@@ -802,7 +810,7 @@ def main():
         clk = clocks.stop()
         # kernel times for the roofline from an eager, instrumented pass
         _, prof = time_steps(g, Us, max(3, min(args.steps, 5)), rk, w.cfl, profile=True)
-        prof = (prof[0], prof[1], prof[2] * args.steps // max(3, min(args.steps, 5)))
+        prof = (prof[0], prof[1], prof[2] * args.steps // max(3, min(args.steps, 5)), prof[3])
     else:
         ms, prof = time_steps(g, Us, args.steps, rk, w.cfl, profile=True)
         clk = clocks.stop()
@@ -812,7 +820,7 @@ def main():
     value = units / (ms / 1e3)
 
     # the dominant kernel: the fused stencil/update kernel
-    st_ms, st_n, k_launches = prof
+    st_ms, st_n, k_launches, by_stage = prof
     per_launch_ms = st_ms / max(st_n, 1)
     peaks, peak_src = measured_peaks()
     form = "fp64" if main_prec == sensei.FP64 else "fp32_flux"
@@ -829,7 +837,7 @@ def main():
             "traffic_source": "ncu DRAM bytes per cell of the 192^3 capture x cells (3-stage average)",
             "kernel": "stencil_kernel<double,double> (fused MUSCL + Roe + residual + RK stage)",
             "peak_source": "derived FP64 vector peak: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz",
-            "alg_flops_per_launch": flops, "kernel_ms_per_launch": per_launch_ms,
+            "alg_flops_per_launch": flops, "kernel_ms_per_launch": per_launch_ms, "kernel_ms_by_stage": by_stage,
             "oracle_ops_per_cell_stage": ORACLE_OPS_PER_CELL_STAGE,
             "hbm": {"achieved_gbs": hbm_gbs, "peak_gbs": peaks["hbm_gbs"], "frac": hbm_gbs / peaks["hbm_gbs"],
                     "peak_source": peak_src, "alg_bytes_per_launch": byts},
@@ -842,7 +850,7 @@ def main():
             "traffic_source": "ncu DRAM bytes per cell of the 192^3 capture x cells (3-stage average)",
             "peak_source": peak_src,
             "kernel": "stencil32p_kernel<double> (paired FP32 MUSCL + Roe on the FP64 state, FP64 update)",
-            "alg_bytes_per_launch": byts, "kernel_ms_per_launch": per_launch_ms,
+            "alg_bytes_per_launch": byts, "kernel_ms_per_launch": per_launch_ms, "kernel_ms_by_stage": by_stage,
             "pipe": pipe_roofline(form, step_flops_per_launch(w.limiter, two_d, cells, stages), per_launch_ms),
         }
 
@@ -920,7 +928,8 @@ def main():
                 "rho_l2_rel_err_vs_fp64": rho_l2, "steps_compared": n_cmp,
                 "roofline": {"bound": "hbm", "achieved": bv / (stv / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": bv / (stv / 1e3) / 1e9 / peaks["hbm_gbs"],
-                             "kernel_ms_per_launch": stv, "alg_bytes_per_launch": bv, "peak_source": peak_src,
+                             "kernel_ms_per_launch": stv, "kernel_ms_by_stage": profv[3],
+                             "alg_bytes_per_launch": bv, "peak_source": peak_src,
                              "pipe": pipe_roofline(vname, step_flops_per_launch(w.limiter, two_d, cells, stages),
                                                    stv)}}
             del gv, Uv

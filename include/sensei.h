@@ -282,6 +282,13 @@ sensei_status sensei_profile_enable(sensei_grid *grid, int enable);
 sensei_status sensei_profile_read(sensei_grid *grid, double *stencil_ms, long long *stencil_launches,
                                   long long *kernel_launches, int reset);
 
+/* The durations in milliseconds of the individual stencil launches timed
+ * since the last reset, in launch order (for a step: one per Runge-Kutta
+ * stage): the first min(cap, *count) go to ms[] (caller-owned host array),
+ * *count receives how many there are.  Synchronises those events; resets
+ * nothing (sensei_profile_read does). */
+sensei_status sensei_profile_launches(sensei_grid *grid, double *ms, int cap, int *count);
+
 /* ---- Heterogeneous CPU + GPU co-execution (Sec. 4 workflow, Sec. 6 Eq.
  * hete, Sec. 7 workload ratio): the cells of one time step split between
  * the GPU and the host cores, the ghost layers of the cut exchanged every

@@ -794,6 +794,25 @@ sensei_status sensei_profile_read(sensei_grid *grid, double *stencil_ms, long lo
     return SENSEI_OK;
 }
 
+sensei_status sensei_profile_launches(sensei_grid *grid, double *ms, int cap, int *count)
+{
+    sensei_status st = check_grid(grid);
+    if (st != SENSEI_OK) return st;
+    if (!count) return fail(SENSEI_ERR_INVALID_ARG, "count is NULL");
+    if (cap < 0 || (cap > 0 && !ms)) return fail(SENSEI_ERR_INVALID_ARG, "ms is NULL or cap < 0");
+    Device dev;
+    CUDA_TRY(dev.set(grid->device));
+    const int n = (int)(grid->ev_used / 2);
+    for (int i = 0; i < n && i < cap; ++i) {
+        CUDA_TRY(cudaEventSynchronize(grid->ev[2 * i + 1]));
+        float t = 0.0f;
+        CUDA_TRY(cudaEventElapsedTime(&t, grid->ev[2 * i], grid->ev[2 * i + 1]));
+        ms[i] = t;
+    }
+    *count = n;
+    return SENSEI_OK;
+}
+
 sensei_status sensei_workspace_size(const sensei_block_desc *blocks, int nblocks, const sensei_scheme *scheme,
                                     size_t *bytes)
 {

@@ -30,7 +30,7 @@ NV = 5
 EXPORTS = ("sensei_workspace_size", "sensei_create_grid", "sensei_destroy_grid", "sensei_state_layout",
            "sensei_set_bc", "sensei_fill_ghosts", "sensei_residual", "sensei_rk_step", "sensei_norms",
            "sensei_rk_step_local", "sensei_step_graph_create", "sensei_step_graph_launch", "sensei_step_graph_destroy", "sensei_autotune",
-           "sensei_profile_enable", "sensei_profile_read", "sensei_residual_norms_noalloc", "sensei_debug_set",
+           "sensei_profile_enable", "sensei_profile_read", "sensei_profile_launches", "sensei_residual_norms_noalloc", "sensei_debug_set",
            "sensei_rk_stage", "sensei_face_exchange", "sensei_dt_min", "sensei_schedule",
            "sensei_host_create", "sensei_host_destroy", "sensei_host_set_bc", "sensei_host_layout",
            "sensei_host_state", "sensei_host_fill_ghosts", "sensei_host_residual", "sensei_host_dt_min",
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
     L.sensei_autotune.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
     L.sensei_profile_enable.argtypes = [vp, C.c_int]
     L.sensei_profile_read.argtypes = [vp, dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
+    L.sensei_profile_launches.argtypes = [vp, dp, C.c_int, C.POINTER(C.c_int)]
     L.sensei_residual_norms_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, dp, vp]
     L.sensei_debug_set.argtypes = [vp, C.c_int, C.c_longlong]
     L.sensei_rk_stage.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_int, C.c_double, vp]
@@ -227,6 +228,15 @@ def sensei_profile_read(grid, reset=True):
     ms, ns, nk = C.c_double(), C.c_longlong(), C.c_longlong()
     _check(load().sensei_profile_read(grid, C.byref(ms), C.byref(ns), C.byref(nk), int(reset)))
     return ms.value, ns.value, nk.value
+
+
+def sensei_profile_launches(grid):
+    """Durations (ms) of the stencil launches timed since the last reset, in order."""
+    n = C.c_int()
+    _check(load().sensei_profile_launches(grid, None, 0, C.byref(n)))
+    buf = (C.c_double * max(n.value, 1))()
+    _check(load().sensei_profile_launches(grid, buf, n.value, C.byref(n)))
+    return list(buf[:n.value])
 
 
 DEBUG_WAIT_LIMIT, DEBUG_TX_EXTRA, DEBUG_ITEM_ORDER = 1, 2, 3
@@ -578,3 +588,6 @@ class Grid:
 
     def profile_read(self, reset=True):
         return sensei_profile_read(self.handle, reset)
+
+    def profile_launches(self):
+        return sensei_profile_launches(self.handle)

@@ -32,3 +32,29 @@ def test_bench_line_has_the_contract_keys():
     assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     clk = line["clocks"]
     assert clk["sm_mhz"] > 0 and clk["sm_max_mhz"] > 0 and isinstance(clk["reasons"], list)
+    # one mean launch time per Runge-Kutta stage, averaging to the per-launch mean
+    by_stage = roof["kernel_ms_by_stage"]
+    assert len(by_stage) == 3 and all(t > 0 for t in by_stage)
+    assert sum(by_stage) / 3 == pytest.approx(roof["kernel_ms_per_launch"], rel=1e-6)
+
+
+def test_profile_launches_lists_each_stencil_launch():
+    import torch
+    from paper_2305_18057_gb300 import sensei, workloads as wl
+    w = wl.periodic_3d(n=32)
+    g = sensei.Grid(w.dims, w.nodes, limiter=sensei.LIM_VANLEER, precision=sensei.FP32_STORE)
+    for f in range(6):
+        g.set_bc(0, f, sensei.BC_PERIODIC)
+    U = [g.new_state(0)]
+    g.upload(U[0], 0, w.U0[0])
+    g.profile(True)
+    g.profile_read(reset=True)
+    for _ in range(2):
+        g.rk_step(U, sensei.RK3_SSP, cfl=0.5)
+    torch.cuda.synchronize()
+    per = g.profile_launches()
+    ms, n, _ = g.profile_read(reset=True)
+    g.profile(False)
+    assert n == 6 and len(per) == 6 and all(t > 0 for t in per)
+    assert sum(per) == pytest.approx(ms, rel=1e-6)
+    assert g.profile_launches() == []
