@@ -222,13 +222,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
             issue_group<TS>(tmap, i0, j0, k0 + 1 + L.gk, nullptr, rawbuf(1), sMet + REC, bar0 + 8, p.tx_extra);
         }
 
-        // FP64 norm partials: double-single sum of squares, FP32 max, FP64
-        // conservation sums (FP64 stage input only)
-        float nsq_hi[NV], nsq_lo[NV], nmax[NV];
+        // norm partials (FP64 stage input only): the sum of squares of the
+        // FP32 residual in FP32 along the thread's column (at most a k-chunk
+        // of 128 terms: relative error below 128 x 2^-24 = 7.6e-6, under the
+        // FP32 residual's own), FP64 across threads and items; FP32 max;
+        // FP64 conservation sums
+        float nsq[NV], nmax[NV];
         double ncons[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            nsq_hi[v] = nsq_lo[v] = nmax[v] = 0.0f;
+            nsq[v] = nmax[v] = 0.0f;
             ncons[v] = 0.0;
         }
 
@@ -516,11 +519,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                         for (int v = 0; v < NV; ++v) {
                             float delta = -c32 * rres[v];
                             if (has_prev) delta = fmaf(beta32, dpv[v], delta);
-                            // float(U^n): the stage input's own conversion on the
-                            // first stage; the hardware conversion (round to
-                            // nearest even, off the integer pipe) on the later
-                            // ones -- the two differ only on exact ties
-                            const float xc = WIDE ? to_f32(uin[v]) : __double2float_rn(unv[v]);
+                            // float(U^n) by the hardware conversion (round to
+                            // nearest even, off the integer pipe), from the
+                            // stage input on the first stage, from U^n later
+                            const float xc = __double2float_rn(WIDE ? uin[v] : unv[v]);
                             dout[cell + v * L.sv] = delta;
                             q32[v] = xc + delta;
                             xout[cell + v * L.sv] = q32[v];
@@ -528,19 +530,22 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                         if (p.push && boundary) push_ghosts<float>(p, B, b, ci, cj, k, q32, NFACES);
                     }
                 } else {
+                    // FP64 stage state: U^(s) = alpha U^n + beta U^(s-1) + coef R
+                    // in FP64 with the FP64 1/|Omega| (the conservation sums
+                    // hold to FP64 round-off)
                     const double coef = MODE != MODE_ACCUM ? 0.0 : p.local ? -p.gdt * dtvd : -p.gdt * dt * ivd;
                     double q64[NV];
                     double *out64 = out_wide ? slot64(B, p.user[b], p.out_slot) : nullptr;
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        double r = to_f64(rres[v]);
-                        if (MODE == MODE_RESIDUAL && p.src[b]) r -= p.src[b][v * nint + rc];
                         if (MODE == MODE_ACCUM) {
-                            double val = p.beta * uin[v] + coef * r;
+                            double val = p.beta * uin[v] + coef * to_f64(rres[v]);
                             if (p.alpha != 0.0) val += p.alpha * unv[v];
                             out64[cell + v * L.sv] = val;
                             q64[v] = val;
                         } else {
+                            double r = to_f64(rres[v]);
+                            if (p.src[b]) r -= p.src[b][v * nint + rc];
                             p.rout[b][v * nint + rc] = r;
                         }
                     }
@@ -557,8 +562,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                             hi = to_f32(r);
                             lo = to_f32(r - to_f64(hi));
                         }
-                        const float sq = hi * hi;
-                        ds_add(nsq_hi[v], nsq_lo[v], sq, fmaf(hi, hi, -sq) + 2.0f * hi * lo);
+                        nsq[v] = fmaf(hi, fmaf(2.0f, lo, hi), nsq[v]);
                         nmax[v] = fmaxf(nmax[v], fabsf(hi + lo));
                         ncons[v] = fma(vold, uin[v], ncons[v]);
                     }
@@ -571,7 +575,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
         if (NORMS) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                double a = (double)nsq_hi[v] + (double)nsq_lo[v], bm = (double)nmax[v], cc = ncons[v];
+                double a = (double)nsq[v], bm = (double)nmax[v], cc = ncons[v];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     a += __shfl_down_sync(0xffffffffu, a, o);
