@@ -197,8 +197,11 @@ cudaError_t launch_stencil_f32s(const BatchParams<float> &p, int limiter, bool t
 // the 3D FP32-arithmetic kernel with paired face fluxes (in_f32: on an FP32 stage state)
 cudaError_t launch_stencil32p(const BatchParams<float> &p, int limiter, bool in_f32, int grid, cudaStream_t s);
 int stencil32p_ctas_per_sm(int limiter, bool in_f32);
-cudaError_t launch_stencil32p_f64in(const BatchParams<float> &p, int limiter, int grid, cudaStream_t s);
-int stencil32p_ctas_per_sm_f64in(int limiter);
+cudaError_t launch_stencil32p_f64in_accum(const BatchParams<float> &p, int limiter, int grid, cudaStream_t s);
+cudaError_t launch_stencil32p_f64in_residual(const BatchParams<float> &p, int limiter, int grid, cudaStream_t s);
+cudaError_t launch_stencil32p_f64in_incr(const BatchParams<float> &p, int limiter, int grid, cudaStream_t s);
+int stencil32p_ctas_per_sm_f64in(int limiter, int mode);
+int stencil32p_ctas_per_sm_f64in_incr(int limiter);
 // double-float arithmetic on an FP64 state
 cudaError_t launch_stencil_df64(const BatchParams<df64> &p, int limiter, bool two_d, int grid, cudaStream_t s);
 int stencil_ctas_per_sm_df64(int limiter, bool two_d);

@@ -122,9 +122,10 @@ __device__ __forceinline__ int halo_cell(int t)
 // step, or a residual); a separate instantiation, so that the other stages
 // do not hold the accumulators' registers.  MODE: the launch's update
 // (MODE_ACCUM, MODE_INCR or MODE_RESIDUAL, the BatchParams field it
-// replaces), fixed at compile time so that each instantiation carries only
-// its own update code and operands.
-template <typename TS, int LIM, bool PART, int MODE>
+// replaces), and LOCAL: local time steps (the BatchParams flag), both
+// fixed at compile time so that each instantiation carries only its own
+// update code and operands.
+template <typename TS, int LIM, bool PART, int MODE, bool LOCAL>
 __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_constant__ BatchParams<float> p)
 {
     using SM = SmemP<TS>;
@@ -433,7 +434,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                     unv[v] = need_un ? un[cell + v * L.sv] : 0.0;
                     dpv[v] = dprev ? dprev[cell + v * L.sv] : 0.0f;
                 }
-                if (p.local) dtvd = B.dtv[mc];
+                if (LOCAL) dtvd = B.dtv[mc];
                 else if (MODE == MODE_ACCUM) ivd = B.ivol[mc];
                 if (NORMS) vold = B.vol[mc];
             }
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                 const long long m0 = (long long)c * ml.mplane + (long long)j0 * ml.mpitch + i0;
                 if (need_un) prefetch_lines(p.user[b] + row0, L.sj * 8, nrow_in, L.sv * 8, NV, row64, t);
                 if (p.dprev >= 0) prefetch_lines(B.ds[p.dprev] + row0 - 2, L.sj * 4, nrow_in, L.sv * 4, NV, len * 4, t);
-                if (MODE == MODE_ACCUM && !p.local)
+                if (MODE == MODE_ACCUM && !LOCAL)
                     prefetch_lines(B.ivol + m0, ml.mpitch * 8, nrow_in, 0, 1, row64, t);
                 if (NORMS) prefetch_lines(B.vol + m0, ml.mpitch * 8, nrow_in, 0, 1, row64, t);
             }
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                 if (MODE == MODE_INCR) {
                     // FP32 increment D = beta Dprev - gdt dt/|Omega| R; X = float(U^n) + D,
                     // or on the last stage U^n + D in FP64
-                    const float c32 = p.local ? gdt32 * to_f32(dtvd) : gdt_dt32 * ivol;
+                    const float c32 = LOCAL ? gdt32 * to_f32(dtvd) : gdt_dt32 * ivol;
                     const bool has_prev = p.dprev >= 0;
                     if (out_wide) {
                         double *out64 = slot64(B, p.user[b], p.out_slot);
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                     // FP64 stage state: U^(s) = alpha U^n + beta U^(s-1) + coef R
                     // in FP64 with the FP64 1/|Omega| (the conservation sums
                     // hold to FP64 round-off)
-                    const double coef = MODE != MODE_ACCUM ? 0.0 : p.local ? -p.gdt * dtvd : -p.gdt * dt * ivd;
+                    const double coef = MODE != MODE_ACCUM ? 0.0 : LOCAL ? -p.gdt * dtvd : -p.gdt * dt * ivd;
                     double q64[NV];
                     double *out64 = out_wide ? slot64(B, p.user[b], p.out_slot) : nullptr;
 #pragma unroll
@@ -602,33 +603,35 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
     }
 }
 
-template <typename TS>
+// Launch of one update mode's instantiations (TS: the stage input's
+// element type); each translation unit instantiates the modes it serves.
+template <typename TS, int MODE>
 struct Stencil32PLauncher {
     using Fn = void (*)(const BatchParams<float>);
-    template <int LIM>
-    static Fn pick_lim(bool part, int mode)
+    template <int LIM, bool PART>
+    static Fn pick_local(bool local)
     {
-        if (sizeof(TS) == 4) {
-            // an FP32 stage input exists only in the later FP32-storage stages
-            return mode == MODE_INCR && !part ? stencil32p_kernel<TS, LIM, false, MODE_INCR> : nullptr;
-        }
-        switch (mode) {
-        case MODE_ACCUM:
-            return part ? stencil32p_kernel<TS, LIM, true, MODE_ACCUM> : stencil32p_kernel<TS, LIM, false, MODE_ACCUM>;
-        case MODE_INCR:
-            return part ? stencil32p_kernel<TS, LIM, true, MODE_INCR> : stencil32p_kernel<TS, LIM, false, MODE_INCR>;
-        case MODE_RESIDUAL:
-            return part ? stencil32p_kernel<TS, LIM, true, MODE_RESIDUAL>
-                        : stencil32p_kernel<TS, LIM, false, MODE_RESIDUAL>;
-        default: return nullptr;
-        }
+        if constexpr (MODE == MODE_RESIDUAL)
+            return stencil32p_kernel<TS, LIM, PART, MODE, false>;   // no time step
+        else
+            return local ? stencil32p_kernel<TS, LIM, PART, MODE, true> : stencil32p_kernel<TS, LIM, PART, MODE, false>;
     }
-    static Fn pick(int limiter, bool part, int mode)
+    template <int LIM>
+    static Fn pick_lim(bool part, bool local)
+    {
+        // an FP32 stage input exists only in the later FP32-storage stages
+        // (no norm partials); norm partials only from an FP64 stage input
+        if constexpr (sizeof(TS) == 4)
+            return part ? nullptr : pick_local<LIM, false>(local);
+        else
+            return part ? pick_local<LIM, true>(local) : pick_local<LIM, false>(local);
+    }
+    static Fn pick(int limiter, bool part, bool local)
     {
         switch (limiter) {
-        case SENSEI_LIM_NONE: return pick_lim<SENSEI_LIM_NONE>(part, mode);
-        case SENSEI_LIM_MINMOD: return pick_lim<SENSEI_LIM_MINMOD>(part, mode);
-        default: return pick_lim<SENSEI_LIM_VANLEER>(part, mode);
+        case SENSEI_LIM_NONE: return pick_lim<SENSEI_LIM_NONE>(part, local);
+        case SENSEI_LIM_MINMOD: return pick_lim<SENSEI_LIM_MINMOD>(part, local);
+        default: return pick_lim<SENSEI_LIM_VANLEER>(part, local);
         }
     }
     static cudaError_t prepare(Fn fn)
@@ -639,22 +642,22 @@ struct Stencil32PLauncher {
     }
     static cudaError_t launch(const BatchParams<float> &p, int limiter, int grid, cudaStream_t s)
     {
-        // norm partials only from an FP64 stage input
-        Fn fn = pick(limiter, sizeof(TS) == 8 && p.partials != nullptr, p.mode);
+        if (p.mode != MODE) return cudaErrorInvalidValue;
+        Fn fn = pick(limiter, p.partials != nullptr, p.local != 0);
         if (!fn) return cudaErrorInvalidValue;
         cudaError_t e = prepare(fn);
         if (e != cudaSuccess) return e;
         fn<<<grid, NTHREADS, SmemP<TS>::bytes, s>>>(p);
         return cudaGetLastError();
     }
-    // the smallest resident CTAs per SM over the instantiations of this
-    // stage input
+    // the smallest resident CTAs per SM over this mode's instantiations
+    // (0 on error, 1 << 30 if it has none)
     static int ctas_per_sm(int limiter)
     {
         int best = 1 << 30;
-        for (int mode : {MODE_ACCUM, MODE_INCR, MODE_RESIDUAL})
-            for (int part = 0; part < 2; ++part) {
-                Fn fn = pick(limiter, part != 0, mode);
+        for (int part = 0; part < 2; ++part)
+            for (int local = 0; local < 2; ++local) {
+                Fn fn = pick(limiter, part != 0, local != 0);
                 if (!fn) continue;
                 if (prepare(fn) != cudaSuccess) return 0;
                 int n = 0;
@@ -662,7 +665,7 @@ struct Stencil32PLauncher {
                     return 0;
                 best = n < best ? n : best;
             }
-        return best == (1 << 30) ? 0 : best;
+        return best;
     }
 };
 

@@ -53,15 +53,28 @@ bool encode_state_map(void *out, const void *base, const BlockDev &B, bool f32)
 }
 
 // the FP32-stage-state instantiations here, the FP64-input ones in
-// stencil_f32pd.cu (two translation units that compile in parallel)
+// stencil_f32pd.cu (accumulating and residual updates) and stencil_f32pe.cu
+// (FP32-storage first stages): translation units that compile in parallel
 cudaError_t launch_stencil32p(const BatchParams<float> &p, int limiter, bool in_f32, int grid, cudaStream_t s)
 {
-    if (in_f32) return Stencil32PLauncher<float>::launch(p, limiter, grid, s);
-    return launch_stencil32p_f64in(p, limiter, grid, s);
+    if (in_f32) return Stencil32PLauncher<float, MODE_INCR>::launch(p, limiter, grid, s);
+    switch (p.mode) {
+    case MODE_ACCUM: return launch_stencil32p_f64in_accum(p, limiter, grid, s);
+    case MODE_RESIDUAL: return launch_stencil32p_f64in_residual(p, limiter, grid, s);
+    case MODE_INCR: return launch_stencil32p_f64in_incr(p, limiter, grid, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 int stencil32p_ctas_per_sm(int limiter, bool in_f32)
 {
-    return in_f32 ? Stencil32PLauncher<float>::ctas_per_sm(limiter) : stencil32p_ctas_per_sm_f64in(limiter);
+    if (in_f32) return Stencil32PLauncher<float, MODE_INCR>::ctas_per_sm(limiter);
+    int best = 1 << 30;
+    for (int m : {MODE_ACCUM, MODE_RESIDUAL, MODE_INCR}) {
+        const int n = stencil32p_ctas_per_sm_f64in(limiter, m);
+        if (n <= 0) return 0;
+        best = n < best ? n : best;
+    }
+    return best;
 }
 }  // namespace sensei

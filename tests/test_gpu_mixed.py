@@ -107,3 +107,27 @@ def test_every_runge_kutta_scheme_in_every_form(precision, rk):
             assert per_var_rel(got, want) < 1e-9, (w.name, rk)
         else:
             assert _l2_rel(got[0], want[0]) <= 1e-5, (w.name, rk)
+
+
+@pytest.mark.parametrize("precision", ["fp32_flux", "fp32_store"])
+@pytest.mark.parametrize("case", ["periodic3d", "lattice"])
+def test_mixed_local_time_stepping_within_target(case, precision):
+    """Local time steps (each cell its own CFL step) in the FP32 forms: the
+    3D FP32 stencil's local-step instantiations against the oracle's local
+    steps, at the mixed forms' state bar."""
+    w = {"periodic3d": lambda: wl.periodic_3d(n=24, nj=16, nk=12, seed=8),
+         "lattice": lambda: wl.lattice_3d(sizes=(6, 9, 13), nblk=(2, 2, 2), seed=4, perturb=0.05)}[case]()
+    og = oracle_grid(w)
+    Uo = oracle_states(og, w)
+    g = gpu_grid(w, precision={"fp32_flux": sensei.FP32_FLUX, "fp32_store": sensei.FP32_STORE}[precision])
+    Us = gpu_states(g, w)
+    for _ in range(30):
+        g.rk_step_local(Us, sensei.RK3_SSP, cfl=0.6)
+        og.rk_step_local(Uo, 1, cfl=0.6)
+    torch.cuda.synchronize()
+    got = np.concatenate([g.download(Us[b], b).reshape(5, -1) for b in range(len(w.dims))], axis=1)
+    want = np.concatenate([og.interior(Uo[b], b).reshape(5, -1) for b in range(len(w.dims))], axis=1)
+    moved = _l2_rel(np.concatenate([og.interior(oracle_states(og, w)[b], b).reshape(5, -1)
+                                    for b in range(len(w.dims))], axis=1)[0], want[0])
+    assert moved > 1e-4, moved
+    assert _l2_rel(got[0], want[0]) <= 1e-5
