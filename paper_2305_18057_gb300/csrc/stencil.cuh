@@ -558,6 +558,98 @@ __device__ __noinline__ void push_ghosts(const BatchParams<R> &p, const BlockDev
     }
 }
 
+// The ghost push of one work item's block in affine form: for each face f,
+// the ghost cell that cell m of the face's line (t1, t2) feeds is element
+// off + t1 a1 + t2 a2 + m a3 of the target array dst (the neighbour's for
+// an interface, the block's own otherwise), variables sv apart.  kind:
+// PUSH_NONE (inflow, caller-written), PUSH_COPY (interface, periodic: the
+// ghost of layer m+1), PUSH_EXTRAP (from the boundary cell into both
+// layers), PUSH_WALL (the mirrored ghost of layer m+1).  Set up once per
+// item by one thread per face (push_face_setup), used by push_affine (NF:
+// the block's faces, 4 in 2D): the same writes as push_ghosts without its
+// per-cell descriptor walk.
+enum { PUSH_NONE = 0, PUSH_COPY = 1, PUSH_EXTRAP = 2, PUSH_WALL = 3 };
+struct PushFace {
+    void *dst;
+    long long off, a1, a2, a3, sv;
+    int kind;
+};
+
+template <typename R>
+__device__ __forceinline__ void push_face_setup(const BatchParams<R> &p, const BlockDev &B, int b, int f,
+                                                PushFace &pf)
+{
+    const int type = B.bc_type[f];
+    const BlockDev *T = &B;
+    double *user = p.user[b];
+    int tf = f;
+    pf.kind = PUSH_NONE;
+    pf.dst = nullptr;
+    pf.off = pf.a1 = pf.a2 = pf.a3 = pf.sv = 0;
+    if (type == SENSEI_BC_INTERFACE) {
+        T = &p.blocks[B.nbr[f]];
+        user = p.user[B.nbr[f]];
+        tf = B.nbr_face[f];
+        pf.kind = PUSH_COPY;
+    } else if (type == SENSEI_BC_PERIODIC) {
+        tf = f ^ 1;
+        pf.kind = PUSH_COPY;
+    } else if (type == SENSEI_BC_EXTRAPOLATE) {
+        pf.kind = PUSH_EXTRAP;
+    } else if (type == SENSEI_BC_SLIP_WALL) {
+        pf.kind = PUSH_WALL;
+    }
+    if (pf.kind == PUSH_NONE) return;
+    pf.dst = p.out_slot >= SLOT_X0 ? (void *)slot32(*T, p.out_slot) : (void *)slot64(*T, user, p.out_slot);
+    int gi, gj, gk, a, c, d;
+    long long e[4];
+    const int probe[4][3] = {{0, 0, 1}, {1, 0, 1}, {0, 1, 1}, {0, 0, 2}};   // (t1, t2, layer)
+    for (int n = 0; n < 4; ++n) {
+        face_cells(tf, T->ni, T->nj, T->nk, probe[n][0], probe[n][1], probe[n][2], 0, gi, gj, gk, a, c, d);
+        e[n] = cell_index(T->L, gi, gj, gk);
+    }
+    pf.off = e[0];
+    pf.a1 = e[1] - e[0];
+    pf.a2 = e[2] - e[0];
+    pf.a3 = e[3] - e[0];
+    pf.sv = T->L.sv;
+}
+
+template <typename T, int NF>
+__device__ __forceinline__ void push_affine(const PushFace *pf, const BlockDev &B, int i, int j, int k,
+                                            const T q[NV])
+{
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const int m = f == 0 ? i : f == 1 ? B.ni - 1 - i : f == 2 ? j : f == 3 ? B.nj - 1 - j : f == 4 ? k
+                                                                                                   : B.nk - 1 - k;
+        const int kind = pf[f].kind;
+        if (m > 1 || kind == PUSH_NONE || (kind == PUSH_EXTRAP && m != 0)) continue;
+        int t1, t2;
+        tangential(f, i, j, k, t1, t2);
+        T *dst = reinterpret_cast<T *>(pf[f].dst);
+        const long long g = pf[f].off + t1 * pf[f].a1 + t2 * pf[f].a2 + m * pf[f].a3, sv = pf[f].sv;
+        if (kind == PUSH_WALL) {
+            double nx, ny, nz;
+            boundary_normal(B, f, t1, t2, nx, ny, nz);
+            const T tx = (T)nx, ty = (T)ny, tz = (T)nz;
+            const T mn = q[1] * tx + q[2] * ty + q[3] * tz;
+            dst[g] = q[0];
+            dst[g + sv] = q[1] - T(2) * mn * tx;
+            dst[g + 2 * sv] = q[2] - T(2) * mn * ty;
+            dst[g + 3 * sv] = q[3] - T(2) * mn * tz;
+            dst[g + 4 * sv] = q[4];
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) dst[g + v * sv] = q[v];
+            if (kind == PUSH_EXTRAP) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) dst[g + pf[f].a3 + v * sv] = q[v];
+            }
+        }
+    }
+}
+
 template <typename R, typename TS, int LIM, bool TWO_D, bool PART>
 __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(const __grid_constant__ BatchParams<R> p)
 {
@@ -571,6 +663,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     R *sK = sFj + SL::FJ;
     double *sRed = reinterpret_cast<double *>(sK + SL::K + ((SL::elems * sizeof(R)) % 8 ? 1 : 0));
     __shared__ BlockDev sB;
+    __shared__ PushFace sPush[6];   // the item's ghost push, face by face
 
     constexpr int WP = TI + 4;                 // sW row pitch
     constexpr int WPL = (TJ + 4) * WP;         // sW variable plane
@@ -602,6 +695,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
             const int *src = reinterpret_cast<const int *>(&p.blocks[b]);
             int *dst = reinterpret_cast<int *>(&sB);
             for (int w = t; w < (int)(sizeof(BlockDev) / sizeof(int)); w += NTHREADS) dst[w] = src[w];
+            if (t < NFACES && p.push) push_face_setup(p, p.blocks[b], b, t, sPush[t]);
         }
         __syncthreads();
         const BlockDev &B = sB;
@@ -868,7 +962,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                             ncons[v] = fma(vol, uin, ncons[v]);
                         }
                     }
-                    if (p.push && boundary && p.mode == MODE_ACCUM) push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
+                    if (p.push && boundary && p.mode == MODE_ACCUM) push_affine<double, NFACES>(sPush, B, ci, cj, k, q64);
                 }
             }
             if (!TWO_D) {

@@ -141,9 +141,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
     double *sRed = reinterpret_cast<double *>(smem + SM::off_red);
     const uint32_t bar0 = smem_addr(smem + SM::off_bar);
     __shared__ BlockDev sB;
+    __shared__ PushFace sPush[6];   // the item's ghost push, face by face
 
     constexpr int FJV = (TJ + 1) * TI;   // sFj variable plane
-    constexpr int NFACES = 6;
 
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
             const int *src = reinterpret_cast<const int *>(&p.blocks[b]);
             int *dst = reinterpret_cast<int *>(&sB);
             for (int w = t; w < (int)(sizeof(BlockDev) / sizeof(int)); w += NTHREADS) dst[w] = src[w];
+            if (t < 6 && p.push) push_face_setup(p, p.blocks[b], b, t, sPush[t]);
         }
         __syncthreads();
         const BlockDev &B = sB;
@@ -511,7 +512,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                             q64[v] = unv[v] + to_f64(delta);
                             out64[cell + v * L.sv] = q64[v];
                         }
-                        if (p.push && boundary) push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
+                        if (p.push && boundary) push_affine<double, 6>(sPush, B, ci, cj, k, q64);
                     } else {
                         float *xout = slot32(B, p.out_slot);
                         float *dout = B.ds[p.dout];
@@ -528,7 +529,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                             q32[v] = xc + delta;
                             xout[cell + v * L.sv] = q32[v];
                         }
-                        if (p.push && boundary) push_ghosts<float>(p, B, b, ci, cj, k, q32, NFACES);
+                        if (p.push && boundary) push_affine<float, 6>(sPush, B, ci, cj, k, q32);
                     }
                 } else {
                     // FP64 stage state: U^(s) = alpha U^n + beta U^(s-1) + coef R
@@ -550,7 +551,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                             p.rout[b][v * nint + rc] = r;
                         }
                     }
-                    if (p.push && boundary && MODE != MODE_RESIDUAL) push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
+                    if (p.push && boundary && MODE != MODE_RESIDUAL) push_affine<double, 6>(sPush, B, ci, cj, k, q64);
                 }
                 if (NORMS) {
 #pragma unroll
