@@ -107,10 +107,10 @@ def alg_bytes_per_cell(form, stage, two_d, stages=3):
 # SSPRK3 stage launches, from ncu dram__bytes_read.sum + dram__bytes_write.sum
 # of the 192^3 case of the periodic 3D workload (profiles/
 # stencil_traffic_periodic3d_192.md for FP64, profiles/
-# stencil32p_traffic_periodic3d_192.md for the FP32 flux form); the same tile
+# stencil32p_traffic_periodic3d_192.md for the FP32 forms); the same tile
 # schedule at 256^3, so the traffic scales with the cells.  Re-measure when
 # the kernel changes.
-MEASURED_TRAFFIC_B_PER_CELL = {"fp64": 226.6, "fp32_flux": 192.1}
+MEASURED_TRAFFIC_B_PER_CELL = {"fp64": 225.2, "fp32_flux": 184.0, "fp32_store": 172.5}
 
 
 def measured_peaks():
@@ -929,6 +929,8 @@ def main():
                 "roofline": {"bound": "hbm", "achieved": bv / (stv / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
                              "unit": "GB/s", "frac": bv / (stv / 1e3) / 1e9 / peaks["hbm_gbs"],
                              "kernel_ms_per_launch": stv, "kernel_ms_by_stage": profv[3],
+                             "traffic": (MEASURED_TRAFFIC_B_PER_CELL[vname] * cells
+                                         if not two_d and vname in MEASURED_TRAFFIC_B_PER_CELL else None),
                              "alg_bytes_per_launch": bv, "peak_source": peak_src,
                              "pipe": pipe_roofline(vname, step_flops_per_launch(w.limiter, two_d, cells, stages),
                                                    stv)}}
