@@ -588,7 +588,8 @@ def _core_boxes(w, margin=6, core=10):
     ni, nj, nk = w.dims[0]
     starts = [(0, 0, 0), (ni - e, nj - e, nk - e), (ni // 2 - e // 2, 3, nk - e - 5), (7, nj // 3, nk // 2)]
     starts = [tuple(max(0, min(a, n - e)) for a, n in zip(st, (ni, nj, nk))) for st in starts]
-    return [(0, st, (st[0] + e, st[1] + e, st[2] + e)) for st in starts]
+    # a 2D block (one plane) keeps its single plane: the box spans k = 0 .. 1
+    return [(0, st, (st[0] + e, st[1] + e, st[2] + e if nk > 1 else 1)) for st in starts]
 
 
 def _oracle_subbox_step(w, b, lo, hi, dt, margin=6):
@@ -611,18 +612,20 @@ def _oracle_subbox_step(w, b, lo, hi, dt, margin=6):
         return r % n if periodic else np.clip(r, 0, n - 1)
 
     per = [faces[2 * d].type == wl.PERIODIC for d in range(3)]
-    ii, jj, kk = rng(i0, i1, ni, per[0]), rng(j0, j1, nj, per[1]), rng(k0, k1, nk, per[2])
+    ii, jj = rng(i0, i1, ni, per[0]), rng(j0, j1, nj, per[1])
+    kk = rng(k0, k1, nk, per[2]) if nk > 1 else np.zeros(1, dtype=np.int64)   # 2D: no k ghosts
     U = np.ascontiguousarray(w.U0[b][:, kk[:, None, None], jj[None, :, None], ii[None, None, :]])
     on_face = [i0 == 0, i1 == ni, j0 == 0, j1 == nj, k0 == 0, k1 == nk]
-    for f in range(6):
+    for f in range(6 if nk > 1 else 4):
         bc = faces[f]
         if on_face[f] and bc.type not in (wl.PERIODIC, wl.INTERFACE):
             g.set_bc(0, f, bc.type, bc.prim)
     g.fill_ghosts([U])
     m = margin
-    before = g.interior(U, 0)[:, m:-m, m:-m, m:-m].copy()
+    ks = slice(m, -m) if nk > 1 else slice(None)
+    before = g.interior(U, 0)[:, ks, m:-m, m:-m].copy()
     g.rk_step([U], oracle.RK3_SSP, dt=dt)
-    return before, g.interior(U, 0)[:, m:-m, m:-m, m:-m].copy()
+    return before, g.interior(U, 0)[:, ks, m:-m, m:-m].copy()
 
 
 def _gpu_one_step(w, precision, boxes, dt, margin=6):
@@ -641,7 +644,8 @@ def _gpu_one_step(w, precision, boxes, dt, margin=6):
     m = margin
     out = []
     for b, lo, hi in boxes:
-        v = g.interior_view(Us[b], b)[:, lo[2] + m:hi[2] - m, lo[1] + m:hi[1] - m, lo[0] + m:hi[0] - m]
+        mk = m if w.dims[b][2] > 1 else 0
+        v = g.interior_view(Us[b], b)[:, lo[2] + mk:hi[2] - mk, lo[1] + m:hi[1] - m, lo[0] + m:hi[0] - m]
         out.append(v.cpu().numpy().copy())
     del g, Us
     torch.cuda.empty_cache()
@@ -686,7 +690,8 @@ def err_vs_oracle(w, forms):
     want = [r[1] for r in res]
     core = [tuple(h - l - 12 for l, h in zip(lo, hi)) for _, lo, hi in boxes]
     sample = (f"one SSPRK3 step (dt {dt:.6g}, the FP64 path's CFL step) from the initial state, on the cores "
-              f"{core[0][0]}^3 of {len(boxes)} sub-boxes (6 margin cells; the oracle on each sub-box with the "
+              f"{core[0][0]}^{3 if w.dims[boxes[0][0]][2] > 1 else 2} of {len(boxes)} sub-boxes (6 margin cells; "
+              f"the oracle on each sub-box with the "
               f"state as the ghosts of its cut faces)")
     out = {}
     for name, prec in forms:
@@ -714,15 +719,23 @@ def oracle_leg(args, w, line, main_prec):
         forms = forms[:2]
     w_err = w
     if args.workload == "c5":
-        # the ramp starts as a uniform inflow, so the sampled cores (away
-        # from the wall) have zero increments: the comparison takes seeded
-        # 5% perturbations of rho, p and u on the same grid
+        # the ramps (3D here, 2D below) start as a uniform inflow, so the
+        # sampled cores (away from the wall) have zero increments: the
+        # comparison takes seeded 5% perturbations of rho, p and u on the
+        # same grid
         from paper_2305_18057_gb300 import workloads as wl
         w_err = wl.ramp_3d(n=w.dims[0][0], perturb=0.05)
+    elif args.workload == "c2":
+        from paper_2305_18057_gb300 import workloads as wl
+        w_err = wl.ramp_2d(ni=w.dims[0][0], nj=w.dims[0][1], perturb=0.05)
+    elif args.workload == "c4":
+        # the lattice's uniform inflow likewise
+        from paper_2305_18057_gb300 import workloads as wl
+        w_err = wl.lattice_3d(perturb=0.05)
     table = err_vs_oracle(w_err, forms)
     if w_err is not w:
         for t in table.values():
-            t["sample"] += "; the ramp's state with seeded 5% perturbations"
+            t["sample"] += "; the workload's state with seeded 5% perturbations"
     main_name = "fp64" if main_prec == sensei.FP64 else "fp32_flux"
     line["err_vs_oracle"] = table[main_name]
     for name, t in table.items():
