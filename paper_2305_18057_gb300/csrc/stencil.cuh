@@ -495,70 +495,14 @@ __device__ __forceinline__ float *out_buffer<float>(const BlockDev &N, double *,
     return slot32(N, slot);
 }
 
-// Write the new value q of interior cell (i, j, k) of block b into every
+// The ghost push: the new value q of a boundary cell is written into every
 // ghost cell it feeds (the ghost rules of the boundary fill, applied from
 // the producing side): interface and periodic ghosts of layer m+1 for the
 // cell m cells inside a face, the mirrored wall ghost of layer m+1, both
-// extrapolation ghosts from the boundary cell.  Inflow ghosts are fixed;
+// extrapolation ghosts from the boundary cell; inflow ghosts are fixed and
 // caller-written (external) ghosts are the caller's.
-template <typename T, typename R>
-__device__ __noinline__ void push_ghosts(const BatchParams<R> &p, const BlockDev &B, int b, int i, int j, int k,
-                                         const T q[NV], int nfaces)
-{
-    for (int f = 0; f < nfaces; ++f) {
-        int m;
-        switch (f) {
-        case 0: m = i; break;
-        case 1: m = B.ni - 1 - i; break;
-        case 2: m = j; break;
-        case 3: m = B.nj - 1 - j; break;
-        case 4: m = k; break;
-        default: m = B.nk - 1 - k; break;
-        }
-        if (m > 1) continue;
-        const int type = B.bc_type[f];
-        if (type == SENSEI_BC_INFLOW || type == SENSEI_BC_EXTERNAL || (type == SENSEI_BC_EXTRAPOLATE && m != 0))
-            continue;
-        int t1, t2;
-        tangential(f, i, j, k, t1, t2);
-        int gi, gj, gk, a, c, d;
-        if (type == SENSEI_BC_INTERFACE) {
-            const int nb = B.nbr[f];
-            const BlockDev &N = p.blocks[nb];
-            T *dst = out_buffer<T>(N, p.user[nb], p.out_slot);
-            face_cells(B.nbr_face[f], N.ni, N.nj, N.nk, t1, t2, m + 1, 0, gi, gj, gk, a, c, d);
-            const long long g = cell_index(N.L, gi, gj, gk);
-            for (int v = 0; v < NV; ++v) dst[g + v * N.L.sv] = q[v];
-            continue;
-        }
-        T *dst = out_buffer<T>(B, p.user[b], p.out_slot);
-        if (type == SENSEI_BC_PERIODIC) {
-            face_cells(f ^ 1, B.ni, B.nj, B.nk, t1, t2, m + 1, 0, gi, gj, gk, a, c, d);
-            const long long g = cell_index(B.L, gi, gj, gk);
-            for (int v = 0; v < NV; ++v) dst[g + v * B.L.sv] = q[v];
-        } else if (type == SENSEI_BC_EXTRAPOLATE) {
-            for (int layer = 1; layer <= 2; ++layer) {
-                face_cells(f, B.ni, B.nj, B.nk, t1, t2, layer, 0, gi, gj, gk, a, c, d);
-                const long long g = cell_index(B.L, gi, gj, gk);
-                for (int v = 0; v < NV; ++v) dst[g + v * B.L.sv] = q[v];
-            }
-        } else {   // slip wall: mirror image
-            double nx, ny, nz;
-            boundary_normal(B, f, t1, t2, nx, ny, nz);
-            const T tx = (T)nx, ty = (T)ny, tz = (T)nz;
-            const T mn = q[1] * tx + q[2] * ty + q[3] * tz;
-            face_cells(f, B.ni, B.nj, B.nk, t1, t2, m + 1, 0, gi, gj, gk, a, c, d);
-            const long long g = cell_index(B.L, gi, gj, gk);
-            dst[g] = q[0];
-            dst[g + B.L.sv] = q[1] - T(2) * mn * tx;
-            dst[g + 2 * B.L.sv] = q[2] - T(2) * mn * ty;
-            dst[g + 3 * B.L.sv] = q[3] - T(2) * mn * tz;
-            dst[g + 4 * B.L.sv] = q[4];
-        }
-    }
-}
-
-// The ghost push of one work item's block in affine form: for each face f,
+//
+// It is held per work item in affine form: for each face f,
 // the ghost cell that cell m of the face's line (t1, t2) feeds is element
 // off + t1 a1 + t2 a2 + m a3 of the target array dst (the neighbour's for
 // an interface, the block's own otherwise), variables sv apart.  kind:
@@ -566,8 +510,8 @@ __device__ __noinline__ void push_ghosts(const BatchParams<R> &p, const BlockDev
 // ghost of layer m+1), PUSH_EXTRAP (from the boundary cell into both
 // layers), PUSH_WALL (the mirrored ghost of layer m+1).  Set up once per
 // item by one thread per face (push_face_setup), used by push_affine (NF:
-// the block's faces, 4 in 2D): the same writes as push_ghosts without its
-// per-cell descriptor walk.
+// the block's faces, 4 in 2D), so that a boundary cell's push is inlined
+// arithmetic with no per-cell walk through the block descriptors.
 enum { PUSH_NONE = 0, PUSH_COPY = 1, PUSH_EXTRAP = 2, PUSH_WALL = 3 };
 struct PushFace {
     void *dst;

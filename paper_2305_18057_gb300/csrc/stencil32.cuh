@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
     double *sRed = reinterpret_cast<double *>(smem + SM::off_red);
     const uint32_t bar0 = smem_addr(smem + SM::off_bar);
     __shared__ BlockDev sB;
+    __shared__ PushFace sPush[6];   // the item's ghost push, face by face
 
     constexpr int FJV = (TJ + 1) * TI;   // sFj variable plane
     constexpr int NFACES = TWO_D ? 4 : 6;
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
             const int *src = reinterpret_cast<const int *>(&p.blocks[b]);
             int *dst = reinterpret_cast<int *>(&sB);
             for (int w = t; w < (int)(sizeof(BlockDev) / sizeof(int)); w += NTHREADS) dst[w] = src[w];
+            if (t < NFACES && p.push) push_face_setup(p, p.blocks[b], b, t, sPush[t]);
         }
         __syncthreads();
         const BlockDev &B = sB;
@@ -542,9 +544,9 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
                     }
                     if (p.push && boundary) {
                         if (out64)
-                            push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
+                            push_affine<double, NFACES>(sPush, B, ci, cj, k, q64);
                         else
-                            push_ghosts<float>(p, B, b, ci, cj, k, q32, NFACES);
+                            push_affine<float, NFACES>(sPush, B, ci, cj, k, q32);
                     }
                 } else {
                     const double coef = p.local ? -p.gdt * dtvd : -p.gdt * dt * ivd;
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(NTHREADS, sizeof(TS) == 4 ? 3 : 2) stencil32_k
                             p.rout[b][v * nint + rc] = r;
                         }
                     }
-                    if (p.push && boundary && p.mode != MODE_RESIDUAL) push_ghosts<double>(p, B, b, ci, cj, k, q64, NFACES);
+                    if (p.push && boundary && p.mode != MODE_RESIDUAL) push_affine<double, NFACES>(sPush, B, ci, cj, k, q64);
                 }
                 if (WIDE && p.partials) {
                     const double vol = vold;
