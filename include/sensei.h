@@ -215,6 +215,18 @@ sensei_status sensei_residual(sensei_grid *grid, double *const *U, double *const
 sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double cfl, double dt,
                              double *dt_used, sensei_stream stream);
 
+/* nsteps >= 1 consecutive sensei_rk_step calls on the same U, with the same
+ * results bit for bit (Eq. runge_kutta; the time-step rule above).  The 3D
+ * FP32-storage form (SENSEI_FP32_STORE) in CFL mode forms each step's CFL
+ * bound in the last Runge-Kutta stage of the step before, from the state it
+ * writes, by the same FP32 arithmetic as the time-step reduction, and skips
+ * that reduction's pass over U (its first step still runs it); so U must
+ * not be changed between the steps, which is what this call guarantees.  dt_used (device, nsteps
+ * doubles, may be NULL) receives each step's dt.  The recorded norms are
+ * those of the last step's first stage. */
+sensei_status sensei_rk_steps(sensei_grid *grid, double *const *U, int nsteps, int rk, double cfl, double dt,
+                              double *dt_used, sensei_stream stream);
+
 /* One step with local time stepping, for marching to a steady state (the
  * paper's inlet case is steady): every cell advances by its own step
  * dt_c = cfl |Omega_c| / sum_d (|u . Sbar_d| + c |Sbar_d|), evaluated on U^n
@@ -245,6 +257,12 @@ sensei_status sensei_norms(sensei_grid *grid, double *l2, double *linf, double *
 typedef struct sensei_step_graph sensei_step_graph;
 sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int rk, double cfl, double dt,
                                        double *dt_used, sensei_stream stream, sensei_step_graph **out);
+/* The same for sensei_rk_steps: one graph of nsteps steps (dt_used: nsteps
+ * doubles or NULL), replayed as a whole; where sensei_rk_steps fuses the
+ * time-step bound, every replay's first step runs the time-step reduction
+ * and the others take the bound of the step before. */
+sensei_status sensei_steps_graph_create(sensei_grid *grid, double *const *U, int nsteps, int rk, double cfl,
+                                        double dt, double *dt_used, sensei_stream stream, sensei_step_graph **out);
 sensei_status sensei_step_graph_launch(sensei_step_graph *graph, sensei_stream stream);
 sensei_status sensei_step_graph_destroy(sensei_step_graph *graph);
 

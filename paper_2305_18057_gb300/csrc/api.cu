@@ -70,7 +70,7 @@ struct Plan {
     std::vector<HostBlock> blocks;
     std::vector<size_t> off_fn, off_fdf, off_rec32, off_vol, off_ivol, off_sbar, off_sbar32, off_dtv, off_stage, off_wv,
         off_rvis, off_fvis, off_gvis, off_tmap;
-    size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtslot = 0, off_norms = 0, off_order = 0;
+    size_t off_desc = 0, off_partials = 0, off_dtbits = 0, off_dtnext = 0, off_dtslot = 0, off_norms = 0, off_order = 0;
     size_t bytes = 0;
     long long max_items = 0;   // partial slots (items at the smallest k-chunk)
     long long ncells = 0;
@@ -231,6 +231,7 @@ sensei_status make_plan(const sensei_block_desc *blocks, int nblocks, const sens
     P.off_partials = take(cur, (size_t)P.max_items * 3 * NV * sizeof(double));
     P.off_order = take(cur, (size_t)P.max_items * sizeof(int));
     P.off_dtbits = take(cur, sizeof(unsigned long long));
+    P.off_dtnext = take(cur, 2 * sizeof(unsigned long long));
     P.off_dtslot = take(cur, sizeof(double));
     P.off_norms = take(cur, 16 * sizeof(double));   // 15 norms + the error word
     P.bytes = round_up((long long)cur, 256);
@@ -272,6 +273,7 @@ struct sensei_grid {
     BlockDev *desc;     // device table
     double *partials;
     unsigned long long *dt_bits;
+    unsigned long long *dt_next;   // two slots: the fused next-step bounds of a multi-step run
     double *dt_slot;
     double *norms;      // 15 doubles, then the error word
     unsigned *err;
@@ -416,6 +418,16 @@ sensei_status fill_slot(sensei_grid *g, int slot, double *const *U, cudaStream_t
 
 bool viscous(const sensei_grid *g) { return g->scheme.mu > 0.0; }
 
+// Grids whose last Runge-Kutta stage forms the next step's time-step bound
+// itself: the 3D FP32-storage form with a global CFL step (its last stage
+// writes U^n + D in FP64; the FP32 rule of the time-step kernel, the same
+// function).  Not the FP32-flux form: there the added work in its FP64-input
+// last stage cost as much as the time-step kernel it saved (measured).
+bool fused_next_dt(const sensei_grid *g, double cfl)
+{
+    return cfl > 0.0 && !g->plan.two_d && !viscous(g) && g->scheme.precision == SENSEI_FP32_STORE;
+}
+
 // The block-edge ghosts of a slot's states (the face ghosts are in place).
 sensei_status fill_edges(sensei_grid *g, int slot, double *const *U, cudaStream_t s)
 {
@@ -484,6 +496,7 @@ struct StencilCall {
     double *const *user;
     double *const *rout;
     const double *const *src;
+    unsigned long long *dt_next;   // the 3D FP32 last stage's fused next-step bound (or null)
 };
 
 template <typename R>
@@ -523,6 +536,8 @@ void fill_params(BatchParams<R> &p, const sensei_grid *g, const StencilCall &c)
     p.dt_scale = c.dt_scale;
     p.partials = c.partials ? g->partials : nullptr;
     p.order = g->order_mode == 1 ? g->order : nullptr;
+    p.dt_next = c.dt_next;
+    p.gamma_d = g->scheme.gamma;
     p.err = g->err;
     for (int b = 0; b < nb; ++b) {
         p.user[b] = c.user ? c.user[b] : nullptr;
@@ -642,15 +657,23 @@ sensei_status prepare_step(sensei_grid *g, double *const *U, cudaStream_t s)
 
 // One RK step, launches only (capturable once prepare_step has run).  With
 // local set every cell advances by its own step cfl |Omega_c| / sum_d(...).
+// dt_in (CFL mode): the bound the previous step's last stage left, which
+// replaces the time-step kernel; dt_out: the slot this step's last stage
+// fills with the next step's bound (both for fused_next_dt grids only).
 sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, double cfl, double dt, double *dt_used,
-                               cudaStream_t s, bool local = false)
+                               cudaStream_t s, bool local = false, const unsigned long long *dt_in = nullptr,
+                               unsigned long long *dt_out = nullptr)
 {
     sensei_status st = fill_slot(grid, SLOT_USER, U, s);
     if (st != SENSEI_OK) return st;
     const double *dt_src;
     double dt_scale;
     const long long nitems = total_items(grid->plan.blocks);
-    if (cfl > 0.0) {
+    if (dt_out) CUDA_TRY(cudaMemsetAsync(dt_out, 0x7F, sizeof(unsigned long long), s));
+    if (cfl > 0.0 && dt_in) {
+        dt_src = (const double *)dt_in;
+        dt_scale = cfl;
+    } else if (cfl > 0.0) {
         CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
         int kchunk = 1;
         for (const HostBlock &H : grid->plan.blocks) kchunk = std::max(kchunk, H.dev.kchunk);
@@ -689,6 +712,7 @@ sensei_status rk_step_launches(sensei_grid *grid, double *const *U, int rk, doub
         c.local = local ? 1 : 0;
         c.dprev = -1;
         c.dout = -1;
+        c.dt_next = last ? dt_out : nullptr;
         if (!incr) {
             // FP64 stage states: U -> ST0 -> ST1 -> ST0 ... -> U
             c.mode = MODE_ACCUM;
@@ -856,6 +880,7 @@ sensei_status sensei_create_grid(const sensei_block_desc *blocks, int nblocks, c
     g->desc = (BlockDev *)(g->ws + P.off_desc);
     g->partials = (double *)(g->ws + P.off_partials);
     g->dt_bits = (unsigned long long *)(g->ws + P.off_dtbits);
+    g->dt_next = (unsigned long long *)(g->ws + P.off_dtnext);
     g->dt_slot = (double *)(g->ws + P.off_dtslot);
     g->norms = (double *)(g->ws + P.off_norms);
     g->order = (int *)(g->ws + P.off_order);
@@ -1082,6 +1107,39 @@ sensei_status sensei_rk_step(sensei_grid *grid, double *const *U, int rk, double
     return st;
 }
 
+// nsteps Runge-Kutta steps, launches only (after prepare_step).  On
+// fused_next_dt grids every step but the last leaves the next step's bound
+// in one of the two dt_next slots and the next step reads it instead of
+// running the time-step kernel: the same dt, one pass over the state fewer.
+sensei_status rk_steps_launches(sensei_grid *grid, double *const *U, int nsteps, int rk, double cfl, double dt,
+                                double *dt_used, cudaStream_t s)
+{
+    const bool fused = fused_next_dt(grid, cfl);
+    for (int n = 0; n < nsteps; ++n) {
+        const unsigned long long *in = fused && n > 0 ? grid->dt_next + (n - 1) % 2 : nullptr;
+        unsigned long long *out = fused && n + 1 < nsteps ? grid->dt_next + n % 2 : nullptr;
+        sensei_status st = rk_step_launches(grid, U, rk, cfl, dt, dt_used ? dt_used + n : nullptr, s, false, in, out);
+        if (st != SENSEI_OK) return st;
+    }
+    return SENSEI_OK;
+}
+
+sensei_status sensei_rk_steps(sensei_grid *grid, double *const *U, int nsteps, int rk, double cfl, double dt,
+                              double *dt_used, sensei_stream stream)
+{
+    TraceRange trace("sensei_rk_steps");
+    sensei_status st = check_step_args(grid, U, rk, cfl, dt);
+    if (st != SENSEI_OK) return st;
+    if (nsteps < 1) return fail(SENSEI_ERR_INVALID_ARG, "nsteps must be at least 1 (got %d)", nsteps);
+    Device dev;
+    CUDA_TRY(dev.set(grid->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    st = prepare_step(grid, U, s);
+    if (st == SENSEI_OK) st = rk_steps_launches(grid, U, nsteps, rk, cfl, dt, dt_used, s);
+    if (st == SENSEI_OK) g_msg[0] = 0;
+    return st;
+}
+
 sensei_status sensei_rk_stage(sensei_grid *grid, double *const *U, int rk, int stage, double dt,
                               sensei_stream stream)
 {
@@ -1197,13 +1255,14 @@ sensei_status sensei_rk_step_local(sensei_grid *grid, double *const *U, int rk, 
     return st;
 }
 
-sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int rk, double cfl, double dt,
-                                       double *dt_used, sensei_stream stream, sensei_step_graph **out)
+static sensei_status steps_graph_create(sensei_grid *grid, double *const *U, int nsteps, int rk, double cfl,
+                                        double dt, double *dt_used, sensei_stream stream, sensei_step_graph **out)
 {
     if (!out) return fail(SENSEI_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     sensei_status st = check_step_args(grid, U, rk, cfl, dt);
     if (st != SENSEI_OK) return st;
+    if (nsteps < 1) return fail(SENSEI_ERR_INVALID_ARG, "nsteps must be at least 1 (got %d)", nsteps);
     Device dev;
     CUDA_TRY(dev.set(grid->device));
     cudaStream_t s = (cudaStream_t)stream;
@@ -1218,7 +1277,7 @@ sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int 
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        st = rk_step_launches(grid, U, rk, cfl, dt, dt_used, cs);
+        st = rk_steps_launches(grid, U, nsteps, rk, cfl, dt, dt_used, cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (st == SENSEI_OK && e2 != cudaSuccess) st = fail(SENSEI_ERR_CUDA, "capture: %s", cudaGetErrorString(e2));
     } else {
@@ -1240,6 +1299,18 @@ sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int 
     *out = gr;
     g_msg[0] = 0;
     return SENSEI_OK;
+}
+
+sensei_status sensei_step_graph_create(sensei_grid *grid, double *const *U, int rk, double cfl, double dt,
+                                       double *dt_used, sensei_stream stream, sensei_step_graph **out)
+{
+    return steps_graph_create(grid, U, 1, rk, cfl, dt, dt_used, stream, out);
+}
+
+sensei_status sensei_steps_graph_create(sensei_grid *grid, double *const *U, int nsteps, int rk, double cfl,
+                                        double dt, double *dt_used, sensei_stream stream, sensei_step_graph **out)
+{
+    return steps_graph_create(grid, U, nsteps, rk, cfl, dt, dt_used, stream, out);
 }
 
 sensei_status sensei_step_graph_launch(sensei_step_graph *graph, sensei_stream stream)

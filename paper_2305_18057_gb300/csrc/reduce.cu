@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include "blocks.cuh"
+#include "dtbound.cuh"
 
 namespace sensei {
 namespace {
@@ -104,6 +105,20 @@ __global__ void __launch_bounds__(NTHREADS) dt_kernel(const BlockDev *blocks, in
         const long long mv = B.ml.mvolume;
         for (int k = k0; k < k1; ++k) {
             const double *c = U + cell_index(B.L, i, j, k);
+            if constexpr (sizeof(R) == 4) {
+                // the FP32 rule (no viscous term in the FP32 forms), shared
+                // with the FP32 stencil's fused bound
+                const long long m = k * B.ml.mplane + j * B.ml.mpitch + i;
+                float isum, bound;
+                if (!dt_cell_f32(B, m, ndir, c[0], c[B.L.sv], c[2 * B.L.sv], c[3 * B.L.sv], c[4 * B.L.sv], gam, gm1,
+                                 isum, bound)) {
+                    bad = true;
+                    continue;
+                }
+                if (local) B.dtv[m] = cfl * (double)isum;
+                best = fminf(best, bound);
+                continue;
+            }
             const R rho = M::cv(c[0]), mx = M::cv(c[B.L.sv]), my = M::cv(c[2 * B.L.sv]), mz = M::cv(c[3 * B.L.sv]),
                     E = M::cv(c[4 * B.L.sv]);
             const R ir = M::rcp(rho);

@@ -148,6 +148,8 @@ struct BatchParams {
     double dt_scale;
     double *partials;       // 15 doubles per item (null: no norms)
     const int *order;       // launch position -> work item (null: block-major); item costs descending
+    unsigned long long *dt_next;   // 3D FP32 last stage: the next step's time-step bound (bits), or null
+    double gamma_d;         // gamma in FP64 (the time-step rule's constants)
     unsigned *err;
     double *user[MAX_BLOCKS];        // the caller's U, per block
     double *rout[MAX_BLOCKS];        // MODE_RESIDUAL: R[5][nk][nj][ni]

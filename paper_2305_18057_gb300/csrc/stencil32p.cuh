@@ -34,6 +34,7 @@
 // flight and leaves.
 #pragma once
 
+#include "dtbound.cuh"
 #include "pair32.cuh"
 #include "stencil32.cuh"
 
@@ -124,8 +125,12 @@ __device__ __forceinline__ int halo_cell(int t)
 // (MODE_ACCUM, MODE_INCR or MODE_RESIDUAL, the BatchParams field it
 // replaces), and LOCAL: local time steps (the BatchParams flag), both
 // fixed at compile time so that each instantiation carries only its own
-// update code and operands.
-template <typename TS, int LIM, bool PART, int MODE, bool LOCAL>
+// update code and operands.  DTN (the last FP32-storage stage of a step
+// with a global CFL step): every cell's next-step time-step bound from the
+// FP64 state just written (the rule of the FP32 time-step kernel, the same
+// function), reduced into p.dt_next, so that the next step needs no
+// time-step kernel.
+template <typename TS, int LIM, bool PART, int MODE, bool LOCAL, bool DTN>
 __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_constant__ BatchParams<float> p)
 {
     using SM = SmemP<TS>;
@@ -161,6 +166,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
     const float gdt_dt32 = (float)(p.gdt * dt);
     const float gdt32 = (float)p.gdt;
     const float beta32 = (float)p.beta;
+    // the next step's bound (DTN): this thread's minimum over its cells
+    const float dgam = (float)p.gamma_d, dgm1 = (float)(p.gamma_d - 1.0);
+    float dtn_best = INFINITY;
+    bool dtn_bad = false;
 
     // the edge face of pair 2: lanes 0..4 of warp w own edge e = 5 w + lane
     // (e < TI: the top j-face of column e; else the right i-face of row
@@ -466,6 +475,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                 if (MODE == MODE_ACCUM && !LOCAL)
                     prefetch_lines(B.ivol + m0, ml.mpitch * 8, nrow_in, 0, 1, row64, t);
                 if (NORMS) prefetch_lines(B.vol + m0, ml.mpitch * 8, nrow_in, 0, 1, row64, t);
+                if (DTN) {
+                    // the next-step bound's metrics: 12 FP32 spectral arrays and |Omega|
+                    const int row32 = min(TI, B.ni - i0) * 4;
+                    prefetch_lines(B.sbar32 + m0, ml.mpitch * 4, nrow_in, ml.mvolume * 4, 12, row32, t);
+                    prefetch_lines(B.vol32 + m0, ml.mpitch * 4, nrow_in, 0, 1, row32, t);
+                }
             }
 
             if (warm) {
@@ -511,6 +526,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
                             if (has_prev) delta = fmaf(beta32, dpv[v], delta);
                             q64[v] = unv[v] + to_f64(delta);
                             out64[cell + v * L.sv] = q64[v];
+                        }
+                        if (DTN) {
+                            float isum, bound;
+                            if (dt_cell_f32(B, mc, 3, q64[0], q64[1], q64[2], q64[3], q64[4], dgam, dgm1, isum, bound))
+                                dtn_best = fminf(dtn_best, bound);
+                            else
+                                dtn_bad = true;
                         }
                         if (p.push && boundary) push_affine<double, 6>(sPush, B, ci, cj, k, q64);
                     } else {
@@ -602,6 +624,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
             }
         }
     }
+
+    // ---- the next step's time-step bound: one atomic minimum per warp on
+    // the bit patterns of the positive doubles (they order like the values)
+    if (DTN) {
+        if (dtn_bad) atomicOr(p.err, ERR_NONPHYSICAL);
+        double bd = (double)dtn_best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bd = fmin(bd, __shfl_down_sync(0xffffffffu, bd, o));
+        if (lane == 0 && bd < INFINITY) atomicMin(p.dt_next, (unsigned long long)__double_as_longlong(bd));
+    }
 }
 
 // Launch of one update mode's instantiations (TS: the stage input's
@@ -609,30 +641,42 @@ __global__ void __launch_bounds__(NTHREADS, 2) stencil32p_kernel(const __grid_co
 template <typename TS, int MODE>
 struct Stencil32PLauncher {
     using Fn = void (*)(const BatchParams<float>);
+    // the fused next-step bound exists for the last FP32-storage stage (an
+    // FP32 stage state in, U^n + D written in FP64, a global step); in the
+    // FP32-flux form's last stage (FP64 input) it cost what it saved
+    // (measured), so that form keeps the time-step kernel
+    static constexpr bool HAS_DTN = MODE == MODE_INCR && sizeof(TS) == 4;
     template <int LIM, bool PART>
-    static Fn pick_local(bool local)
+    static Fn pick_local(bool local, bool dtn)
     {
-        if constexpr (MODE == MODE_RESIDUAL)
-            return stencil32p_kernel<TS, LIM, PART, MODE, false>;   // no time step
-        else
-            return local ? stencil32p_kernel<TS, LIM, PART, MODE, true> : stencil32p_kernel<TS, LIM, PART, MODE, false>;
+        if constexpr (MODE == MODE_RESIDUAL) {
+            return dtn ? nullptr : stencil32p_kernel<TS, LIM, PART, MODE, false, false>;   // no time step
+        } else if constexpr (HAS_DTN && !PART) {
+            if (dtn) return local ? nullptr : stencil32p_kernel<TS, LIM, PART, MODE, false, true>;
+            return local ? stencil32p_kernel<TS, LIM, PART, MODE, true, false>
+                         : stencil32p_kernel<TS, LIM, PART, MODE, false, false>;
+        } else {
+            if (dtn) return nullptr;
+            return local ? stencil32p_kernel<TS, LIM, PART, MODE, true, false>
+                         : stencil32p_kernel<TS, LIM, PART, MODE, false, false>;
+        }
     }
     template <int LIM>
-    static Fn pick_lim(bool part, bool local)
+    static Fn pick_lim(bool part, bool local, bool dtn)
     {
         // an FP32 stage input exists only in the later FP32-storage stages
         // (no norm partials); norm partials only from an FP64 stage input
         if constexpr (sizeof(TS) == 4)
-            return part ? nullptr : pick_local<LIM, false>(local);
+            return part ? nullptr : pick_local<LIM, false>(local, dtn);
         else
-            return part ? pick_local<LIM, true>(local) : pick_local<LIM, false>(local);
+            return part ? pick_local<LIM, true>(local, dtn) : pick_local<LIM, false>(local, dtn);
     }
-    static Fn pick(int limiter, bool part, bool local)
+    static Fn pick(int limiter, bool part, bool local, bool dtn = false)
     {
         switch (limiter) {
-        case SENSEI_LIM_NONE: return pick_lim<SENSEI_LIM_NONE>(part, local);
-        case SENSEI_LIM_MINMOD: return pick_lim<SENSEI_LIM_MINMOD>(part, local);
-        default: return pick_lim<SENSEI_LIM_VANLEER>(part, local);
+        case SENSEI_LIM_NONE: return pick_lim<SENSEI_LIM_NONE>(part, local, dtn);
+        case SENSEI_LIM_MINMOD: return pick_lim<SENSEI_LIM_MINMOD>(part, local, dtn);
+        default: return pick_lim<SENSEI_LIM_VANLEER>(part, local, dtn);
         }
     }
     static cudaError_t prepare(Fn fn)
@@ -644,7 +688,7 @@ struct Stencil32PLauncher {
     static cudaError_t launch(const BatchParams<float> &p, int limiter, int grid, cudaStream_t s)
     {
         if (p.mode != MODE) return cudaErrorInvalidValue;
-        Fn fn = pick(limiter, p.partials != nullptr, p.local != 0);
+        Fn fn = pick(limiter, p.partials != nullptr, p.local != 0, p.dt_next != nullptr);
         if (!fn) return cudaErrorInvalidValue;
         cudaError_t e = prepare(fn);
         if (e != cudaSuccess) return e;
@@ -657,8 +701,9 @@ struct Stencil32PLauncher {
     {
         int best = 1 << 30;
         for (int part = 0; part < 2; ++part)
-            for (int local = 0; local < 2; ++local) {
-                Fn fn = pick(limiter, part != 0, local != 0);
+            for (int local = 0; local < 3; ++local) {
+                // local: 0, 1 (local steps), 2 (the fused next-step bound)
+                Fn fn = pick(limiter, part != 0, local == 1, local == 2);
                 if (!fn) continue;
                 if (prepare(fn) != cudaSuccess) return 0;
                 int n = 0;

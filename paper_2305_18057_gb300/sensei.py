@@ -29,7 +29,7 @@ NV = 5
 # every symbol include/sensei.h declares
 EXPORTS = ("sensei_workspace_size", "sensei_create_grid", "sensei_destroy_grid", "sensei_state_layout",
            "sensei_set_bc", "sensei_fill_ghosts", "sensei_residual", "sensei_rk_step", "sensei_norms",
-           "sensei_rk_step_local", "sensei_step_graph_create", "sensei_step_graph_launch", "sensei_step_graph_destroy", "sensei_autotune",
+           "sensei_rk_step_local", "sensei_rk_steps", "sensei_step_graph_create", "sensei_steps_graph_create", "sensei_step_graph_launch", "sensei_step_graph_destroy", "sensei_autotune",
            "sensei_profile_enable", "sensei_profile_read", "sensei_profile_launches", "sensei_residual_norms_noalloc", "sensei_debug_set",
            "sensei_rk_stage", "sensei_face_exchange", "sensei_dt_min", "sensei_schedule",
            "sensei_host_create", "sensei_host_destroy", "sensei_host_set_bc", "sensei_host_layout",
@@ -88,6 +88,9 @@ def load(path: str = LIB_PATH):
     L.sensei_rk_step_local.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_double, vp, vp]
     L.sensei_step_graph_create.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_double, C.c_double, vp, vp,
                                            C.POINTER(vp)]
+    L.sensei_rk_steps.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_int, C.c_double, C.c_double, vp, vp]
+    L.sensei_steps_graph_create.argtypes = [vp, C.POINTER(vp), C.c_int, C.c_int, C.c_double, C.c_double, vp, vp,
+                                            C.POINTER(vp)]
     L.sensei_step_graph_launch.argtypes = [vp, vp]
     L.sensei_step_graph_destroy.argtypes = [vp]
     L.sensei_autotune.argtypes = [vp, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(C.c_int), vp]
@@ -201,6 +204,17 @@ def sensei_step_graph_create(grid, U_ptrs, rk, cfl, dt, dt_used_ptr, stream_ptr)
     out = C.c_void_p()
     _check(load().sensei_step_graph_create(grid, _ptrs(U_ptrs), rk, cfl, dt, dt_used_ptr, stream_ptr,
                                            C.byref(out)))
+    return out.value
+
+
+def sensei_rk_steps(grid, U_ptrs, nsteps, rk, cfl, dt, dt_used_ptr, stream_ptr):
+    return _check(load().sensei_rk_steps(grid, _ptrs(U_ptrs), nsteps, rk, cfl, dt, dt_used_ptr, stream_ptr))
+
+
+def sensei_steps_graph_create(grid, U_ptrs, nsteps, rk, cfl, dt, dt_used_ptr, stream_ptr):
+    out = C.c_void_p()
+    _check(load().sensei_steps_graph_create(grid, _ptrs(U_ptrs), nsteps, rk, cfl, dt, dt_used_ptr, stream_ptr,
+                                            C.byref(out)))
     return out.value
 
 
@@ -561,6 +575,11 @@ class Grid:
         sensei_rk_step(self.handle, [U.data_ptr() for U in Us], rk, cfl, dt,
                        dt_used.data_ptr() if dt_used is not None else None, self.sptr)
 
+    def rk_steps(self, Us, nsteps, rk=RK3_SSP, cfl=0.5, dt=0.0, dt_used=None):
+        """nsteps rk_step calls in one (dt_used: a device tensor of nsteps doubles)."""
+        sensei_rk_steps(self.handle, [U.data_ptr() for U in Us], nsteps, rk, cfl, dt,
+                        dt_used.data_ptr() if dt_used is not None else None, self.sptr)
+
     def norms(self, check=True):
         return sensei_norms(self.handle, self.sptr, check=check)
 
@@ -572,6 +591,12 @@ class Grid:
         """A replayable CUDA graph of one rk_step on these states."""
         h = sensei_step_graph_create(self.handle, [U.data_ptr() for U in Us], rk, cfl, dt,
                                      dt_used.data_ptr() if dt_used is not None else None, self.sptr)
+        return StepGraph(h, self)
+
+    def steps_graph(self, Us, nsteps, rk=RK3_SSP, cfl=0.5, dt=0.0, dt_used=None):
+        """A replayable CUDA graph of rk_steps(nsteps) on these states."""
+        h = sensei_steps_graph_create(self.handle, [U.data_ptr() for U in Us], nsteps, rk, cfl, dt,
+                                      dt_used.data_ptr() if dt_used is not None else None, self.sptr)
         return StepGraph(h, self)
 
     def autotune(self, Us):
