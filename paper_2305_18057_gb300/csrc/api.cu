@@ -760,6 +760,33 @@ sensei_status check_step_args(sensei_grid *grid, double *const *U, int rk, doubl
 
 }  // namespace
 
+// The CFL minimum over the grid's cells, |Omega| / sum_d (...) without the
+// cfl factor, copied to the host address min_out (pinned for the copy to
+// stay asynchronous) on `stream`; the caller synchronises.  The first half of
+// sensei_dt_min, for drivers that overlap it with host work.
+sensei_status sensei::dt_min_launch(sensei_grid *grid, double *const *U, double *min_out, cudaStream_t s)
+{
+    sensei_status st = check_grid(grid);
+    if (st == SENSEI_OK) st = check_states(grid, U, "U");
+    if (st != SENSEI_OK) return st;
+    if (!min_out) return fail(SENSEI_ERR_INVALID_ARG, "no output");
+    Device dev;
+    CUDA_TRY(dev.set(grid->device));
+    st = sync_descriptors(grid, s);
+    if (st != SENSEI_OK) return st;
+    const long long nitems = total_items(grid->plan.blocks);
+    int kchunk = 1;
+    for (const HostBlock &H : grid->plan.blocks) kchunk = std::max(kchunk, H.dev.kchunk);
+    CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
+    CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, 0, 1.0,
+                       grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms), kchunk,
+                       grid->scheme.precision == SENSEI_FP32_FLUX || grid->scheme.precision == SENSEI_FP32_STORE,
+                       viscous_dt_factor(grid), s));
+    grid->kernel_launches++;
+    CUDA_TRY(cudaMemcpyAsync(min_out, grid->dt_bits, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return SENSEI_OK;
+}
+
 extern "C" {
 
 const char *sensei_last_error(void) { return g_msg; }
@@ -1213,27 +1240,11 @@ sensei_status sensei_face_exchange(sensei_grid *grid, double *const *U, int bloc
 
 sensei_status sensei_dt_min(sensei_grid *grid, double *const *U, double cfl, double *dt_out, sensei_stream stream)
 {
-    sensei_status st = check_grid(grid);
-    if (st == SENSEI_OK) st = check_states(grid, U, "U");
-    if (st != SENSEI_OK) return st;
     if (!dt_out || !(cfl > 0.0)) return fail(SENSEI_ERR_INVALID_ARG, "need cfl > 0 and an output");
-    Device dev;
-    CUDA_TRY(dev.set(grid->device));
-    cudaStream_t s = (cudaStream_t)stream;
-    st = sync_descriptors(grid, s);
-    if (st != SENSEI_OK) return st;
-    const long long nitems = total_items(grid->plan.blocks);
-    int kchunk = 1;
-    for (const HostBlock &H : grid->plan.blocks) kchunk = std::max(kchunk, H.dev.kchunk);
-    CUDA_TRY(cudaMemsetAsync(grid->dt_bits, 0x7F, sizeof(unsigned long long), s));
-    CUDA_TRY(launch_dt(grid->desc, (int)grid->plan.blocks.size(), nitems, U, grid->scheme.gamma, 0, cfl,
-                       grid->dt_bits, grid->err, (int)std::min<long long>(nitems, 8LL * grid->sms), kchunk,
-                       grid->scheme.precision == SENSEI_FP32_FLUX || grid->scheme.precision == SENSEI_FP32_STORE,
-                       viscous_dt_factor(grid), s));
-    grid->kernel_launches++;
     double m = 0.0;
-    CUDA_TRY(cudaMemcpyAsync(&m, grid->dt_bits, sizeof m, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    sensei_status st = dt_min_launch(grid, U, &m, (cudaStream_t)stream);
+    if (st != SENSEI_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     *dt_out = cfl * m;
     g_msg[0] = 0;
     return SENSEI_OK;

@@ -35,6 +35,7 @@ struct sensei_hetero {
     double *xdev[2] = {};           // device buffers
     double *pin_out[2] = {};        // GPU layers, pinned
     double *pin_in[2] = {};         // host layers, pinned
+    double *pin_dt = nullptr;       // the GPU part's CFL minimum, pinned
     cudaStream_t s = nullptr;
     cudaEvent_t ev[4] = {};
     ~sensei_hetero()
@@ -45,6 +46,7 @@ struct sensei_hetero {
             if (pin_out[n]) cudaFreeHost(pin_out[n]);
             if (pin_in[n]) cudaFreeHost(pin_in[n]);
         }
+        if (pin_dt) cudaFreeHost(pin_dt);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -234,6 +236,8 @@ sensei_status sensei_hetero_create(const sensei_block_desc *block, const double 
             cudaHostAlloc((void **)&x->pin_in[n], x->xcount * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
             st = fail_status(SENSEI_ERR_CUDA, "pinned exchange buffers");
     }
+    if (st == SENSEI_OK && cudaHostAlloc((void **)&x->pin_dt, sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+        st = fail_status(SENSEI_ERR_CUDA, "pinned time-step slot");
     for (int n = 0; n < 4 && st == SENSEI_OK; ++n)
         if (cudaEventCreate(&x->ev[n]) != cudaSuccess) st = fail_status(SENSEI_ERR_CUDA, "events");
     if (st != SENSEI_OK) {
@@ -289,10 +293,13 @@ sensei_status sensei_hetero_step(sensei_hetero *x, int rk, double cfl, double dt
     const auto t0 = std::chrono::steady_clock::now();
     sensei_status st = SENSEI_OK;
     if (cfl > 0.0) {
-        double dg = 0.0, dh = 0.0;
-        st = sensei_dt_min(x->g, &x->U_dev, cfl, &dg, x->s);
+        // the GPU part's minimum in flight while the host cores take theirs
+        double dh = 0.0;
+        st = sensei::dt_min_launch(x->g, &x->U_dev, x->pin_dt, x->s);
         if (st == SENSEI_OK) st = sensei_host_dt_min(x->h, cfl, &dh);
         if (st != SENSEI_OK) return st;
+        if (cudaStreamSynchronize(x->s) != cudaSuccess) return fail_status(SENSEI_ERR_CUDA, "GPU time-step minimum");
+        const double dg = cfl * *x->pin_dt;
         dt = std::min(dg, dh);
     }
     if (!(dt > 0.0)) return fail_status(SENSEI_ERR_INVALID_ARG, "need cfl > 0 or dt > 0");
@@ -325,13 +332,15 @@ sensei_status sensei_hetero_step(sensei_hetero *x, int rk, double cfl, double dt
         wait_ms += ms_since(tw);
         float g = 0.0f;
         if (cudaEventElapsedTime(&g, x->ev[0], x->ev[1]) == cudaSuccess) gpu_ms += g;
+        // the host's layers to the device first (asynchronous), then the
+        // GPU's into the host ghosts while that copy runs
         for (int n = 0; n < x->nx && st == SENSEI_OK; ++n) {
-            st = sensei_host_face_exchange(x->h, next, x->hface[n], x->pin_out[n], 1);
-            if (st == SENSEI_OK &&
-                cudaMemcpyAsync(x->xdev[n], x->pin_in[n], bytes, cudaMemcpyHostToDevice, x->s) != cudaSuccess)
+            if (cudaMemcpyAsync(x->xdev[n], x->pin_in[n], bytes, cudaMemcpyHostToDevice, x->s) != cudaSuccess)
                 st = fail_status(SENSEI_ERR_CUDA, "cut layers to the device");
             if (st == SENSEI_OK) st = sensei_face_exchange(x->g, &x->U_dev, 0, next, x->gface[n], x->xdev[n], 1, x->s);
         }
+        for (int n = 0; n < x->nx && st == SENSEI_OK; ++n)
+            st = sensei_host_face_exchange(x->h, next, x->hface[n], x->pin_out[n], 1);
     }
     if (st != SENSEI_OK) return st;
     if (cudaStreamSynchronize(x->s) != cudaSuccess) return fail_status(SENSEI_ERR_CUDA, "end of step");

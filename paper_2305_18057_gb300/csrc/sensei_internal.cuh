@@ -238,6 +238,11 @@ sensei_status fail_status(sensei_status st, const char *fmt, ...);
 bool encode_state_map(void *out, const void *base, const BlockDev &B, bool f32);
 constexpr int TMAP_BYTES = 128;
 
+// The grid's CFL minimum (without the cfl factor) into host memory min_out,
+// asynchronously on stream s (api.cu; the co-execution driver overlaps it
+// with the host worker's minimum)
+sensei_status dt_min_launch(sensei_grid *grid, double *const *U, double *min_out, cudaStream_t s);
+
 cudaError_t launch_norms_finalize(const double *partials, int nparts, long long ncells, double *out15,
                                   cudaStream_t s);
 
