@@ -594,9 +594,17 @@ __device__ __forceinline__ void push_affine(const PushFace *pf, const BlockDev &
     }
 }
 
-template <typename R, typename TS, int LIM, bool TWO_D, bool PART>
+// PLAIN: a Runge-Kutta stage of the Euler equations with one global step
+// (the accumulating update, no local steps, no viscous residual), the
+// stencil's common case, with those runtime choices fixed at compile time so
+// that it carries none of the others' code (fewer registers and spills); the
+// general instantiation serves residuals, local steps and viscous grids.
+template <typename R, typename TS, int LIM, bool TWO_D, bool PART, bool PLAIN>
 __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(const __grid_constant__ BatchParams<R> p)
 {
+    const int mode = PLAIN ? MODE_ACCUM : p.mode;
+    const bool local_dt = PLAIN ? false : p.local != 0;
+    const bool vis = PLAIN ? false : p.vis != 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SL = SmemLayout<R>;
     R *sW = reinterpret_cast<R *>(smem_raw);
@@ -627,7 +635,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
     const R c2 = p.eps * (R(1) + p.kappa) / R(4);
     const R half_eps = p.eps / R(2);
     const int cons = p.cons;
-    const bool update = p.mode != MODE_RESIDUAL;
+    const bool update = mode != MODE_RESIDUAL;
     const double dt = update ? p.dt_scale * *p.dt_slot : 0.0;
 
     // persistent: CTA x takes items x, x + grid, x + 2 grid, ...
@@ -661,7 +669,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                            ? reinterpret_cast<const TS *>(slot32(B, p.in_slot))
                            : reinterpret_cast<const TS *>(slot64(B, p.user[b], p.in_slot));
         const double *un = p.user[b];
-        double *out64 = p.mode == MODE_ACCUM ? slot64(B, p.user[b], p.out_slot) : nullptr;
+        double *out64 = mode == MODE_ACCUM ? slot64(B, p.user[b], p.out_slot) : nullptr;
         CellLoader<R, TS> ld{in, L, B.ni, B.nj, B.nk};
 
         // per-thread FP64 norm accumulators (touched once per plane; under
@@ -882,17 +890,17 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                 {
                     const double ivol = B.ivol[mc];
                     const double vol = B.vol[mc];
-                    const double coef = p.local ? -p.gdt * B.dtv[mc] : -p.gdt * dt * ivol;
+                    const double coef = local_dt ? -p.gdt * B.dtv[mc] : -p.gdt * dt * ivol;
                     const long long rc = ((long long)k * B.nj + cj) * B.ni + ci;
                     const long long nint = (long long)B.ni * B.nj * B.nk;
                     double q64[NV];
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
                         double r = cvt<double, R>(rres[v]);
-                        if (p.vis) r -= B.rvis[v * nint + rc];   // R = sum (F_i - F_nu) . S
-                        if (p.mode == MODE_RESIDUAL && p.src[b]) r -= p.src[b][v * nint + rc];
+                        if (vis) r -= B.rvis[v * nint + rc];   // R = sum (F_i - F_nu) . S
+                        if (mode == MODE_RESIDUAL && p.src[b]) r -= p.src[b][v * nint + rc];
                         const double uin = cvt<double, TS>(in[cell + v * L.sv]);
-                        if (p.mode == MODE_ACCUM) {
+                        if (mode == MODE_ACCUM) {
                             double val = p.beta * uin + coef * r;
                             if (p.alpha != 0.0) val += p.alpha * un[cell + v * L.sv];
                             out64[cell + v * L.sv] = val;
@@ -906,7 +914,7 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
                             ncons[v] = fma(vol, uin, ncons[v]);
                         }
                     }
-                    if (p.push && boundary && p.mode == MODE_ACCUM) push_affine<double, NFACES>(sPush, B, ci, cj, k, q64);
+                    if (p.push && boundary && mode == MODE_ACCUM) push_affine<double, NFACES>(sPush, B, ci, cj, k, q64);
                 }
             }
             if (!TWO_D) {
@@ -963,17 +971,24 @@ __global__ void __launch_bounds__(NTHREADS, MinCtas<R>::value) stencil_kernel(co
 template <typename R, typename TS, bool PART>
 struct StencilLauncher {
     using Fn = void (*)(const BatchParams<R>);
-    static Fn pick(int limiter, bool two_d)
+    template <bool PLAIN>
+    static Fn pick_plain(int limiter, bool two_d)
     {
         switch (limiter) {
-        case SENSEI_LIM_NONE: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_NONE, true, PART>
-                                           : stencil_kernel<R, TS, SENSEI_LIM_NONE, false, PART>;
-        case SENSEI_LIM_MINMOD: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_MINMOD, true, PART>
-                                             : stencil_kernel<R, TS, SENSEI_LIM_MINMOD, false, PART>;
-        default: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_VANLEER, true, PART>
-                              : stencil_kernel<R, TS, SENSEI_LIM_VANLEER, false, PART>;
+        case SENSEI_LIM_NONE: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_NONE, true, PART, PLAIN>
+                                           : stencil_kernel<R, TS, SENSEI_LIM_NONE, false, PART, PLAIN>;
+        case SENSEI_LIM_MINMOD: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_MINMOD, true, PART, PLAIN>
+                                             : stencil_kernel<R, TS, SENSEI_LIM_MINMOD, false, PART, PLAIN>;
+        default: return two_d ? stencil_kernel<R, TS, SENSEI_LIM_VANLEER, true, PART, PLAIN>
+                              : stencil_kernel<R, TS, SENSEI_LIM_VANLEER, false, PART, PLAIN>;
         }
     }
+    static Fn pick(int limiter, bool two_d, bool plain)
+    {
+        return plain ? pick_plain<true>(limiter, two_d) : pick_plain<false>(limiter, two_d);
+    }
+    // a Runge-Kutta stage of the Euler equations with one global step
+    static bool plain(const BatchParams<R> &p) { return p.mode == MODE_ACCUM && !p.local && !p.vis; }
     static cudaError_t prepare(Fn fn)
     {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -985,20 +1000,25 @@ struct StencilLauncher {
     }
     static cudaError_t launch(const BatchParams<R> &p, int limiter, bool two_d, int grid, cudaStream_t s)
     {
-        Fn fn = pick(limiter, two_d);
+        Fn fn = pick(limiter, two_d, plain(p));
         cudaError_t e = prepare(fn);
         if (e != cudaSuccess) return e;
         fn<<<grid, NTHREADS, SmemLayout<R>::bytes, s>>>(p);
         return cudaGetLastError();
     }
+    // the smaller of the plain and the general instantiation's resident CTAs
     static int ctas_per_sm(int limiter, bool two_d)
     {
-        Fn fn = pick(limiter, two_d);
-        if (prepare(fn) != cudaSuccess) return 0;
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NTHREADS, SmemLayout<R>::bytes) != cudaSuccess)
-            return 0;
-        return n;
+        int best = 1 << 30;
+        for (int pl = 0; pl < 2; ++pl) {
+            Fn fn = pick(limiter, two_d, pl != 0);
+            if (prepare(fn) != cudaSuccess) return 0;
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, NTHREADS, SmemLayout<R>::bytes) != cudaSuccess)
+                return 0;
+            best = n < best ? n : best;
+        }
+        return best;
     }
 };
 
