@@ -76,6 +76,26 @@ def test_steps_graph_equals_rk_steps_bitwise(precision):
     assert np.array_equal(n1, n2)
 
 
+@pytest.mark.parametrize("rk", [sensei.RK2_SSP, sensei.RK4_SSP2])
+def test_rk_steps_other_schemes_and_a_given_dt(rk):
+    """The fused bound in two- and four-stage schemes (its last stage is the
+    second or the fourth), and a given dt (no bound at all), both bitwise."""
+    w = CASES["periodic3d"]()
+    for cfl, dt in ((0.5, 0.0), (0.0, 2e-4)):
+        out = []
+        for how in ("single", "multi"):
+            g = gpu_grid(w, precision=sensei.FP32_STORE)
+            Us = gpu_states(g, w)
+            if how == "single":
+                for _ in range(4):
+                    g.rk_step(Us, rk, cfl=cfl, dt=dt)
+            else:
+                g.rk_steps(Us, 4, rk, cfl=cfl, dt=dt)
+            torch.cuda.synchronize()
+            out.append(g.download(Us[0], 0))
+        assert np.array_equal(out[0], out[1]), (rk, cfl)
+
+
 def test_rk_steps_rejects_no_steps():
     w = CASES["periodic3d"]()
     g = gpu_grid(w, precision=sensei.FP32_FLUX)
