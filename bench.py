@@ -418,8 +418,8 @@ def config_for(name):
 def lattice_variant(args, peaks, peak_src, world):
     """The batched multiblock form inside the default run: the 64-block
     lattice (uneven blocks, interface ghost exchange) in FP32 flux on the
-    FP64 state, one batched launch per RK stage over all blocks, a CUDA graph
-    per step, autotuned schedule; beside it the plain FP64 form on the same
+    FP64 state, one batched launch per RK stage over all blocks, one CUDA
+    graph of the timed steps, autotuned schedule; beside it the plain FP64 form on the same
     lattice (its speedup) and the density error against it after the same
     steps from the same state."""
     from paper_2305_18057_gb300 import workloads as wl
@@ -430,9 +430,9 @@ def lattice_variant(args, peaks, peak_src, world):
 
 def ramp_variant(args, peaks, peak_src, world):
     """The 512^3 Mach-4 ramp (one block, wall / inflow / outflow rules,
-    stretched grid) inside the default run: the FP32-storage form, a CUDA
-    graph per step, autotuned schedule; beside it the FP64 form (its speedup
-    and the density error against it)."""
+    stretched grid) inside the default run: the FP32-storage form, one CUDA
+    graph of the timed steps, autotuned schedule; beside it the FP64 form
+    (its speedup and the density error against it)."""
     from paper_2305_18057_gb300 import workloads as wl
     out = workload_variant(args, peaks, peak_src, world, wl.ramp_3d(n=512), "fp32_store", 5)
     out["workload"] = WORKLOADS["c5"]
