@@ -744,6 +744,14 @@ def oracle_leg(args, w, line, main_prec):
     for name, t in table.items():
         if name in line.get("variants", {}):
             line["variants"][name]["err_vs_oracle"] = t
+    vis = line.get("variants", {}).get("fp64_viscous")
+    if vis is not None:
+        # the Navier-Stokes form against the oracle's viscous flux, same sampling
+        import dataclasses
+        wv = dataclasses.replace(w_err, mu=vis["mu"], prandtl=vis["prandtl"])
+        tv = err_vs_oracle(wv, [("fp64_viscous", sensei.FP64)])["fp64_viscous"]
+        tv["sample"] += "; the Navier-Stokes form (mu of Re 1000)"
+        vis["err_vs_oracle"] = tv
     if "c4_lattice" in line.get("variants", {}):
         # the lattice's initial state is a uniform inflow, whose residual
         # vanishes inside the blocks: the comparison takes it with seeded 5%
